@@ -1,0 +1,254 @@
+"""FP64 CPU oracle for spectral correlation density (SCD) estimation: FAM and SSCA.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain reference that the CUDA
+path is checked against.  Only the test suite, the smoke check of the package entry
+file and the CPU-baseline leg of the benchmark may import it; the library never does,
+and it imports nothing from the library.  It shares no code with the CUDA path.
+
+Everything is complex128 / float64.  Inputs arrive as complex64 signals and float32
+windows (the same bits the GPU sees) and are promoted, so a parity check measures only
+the GPU's arithmetic error.  Two modes share nothing but the index conventions:
+
+  * mode="direct": every DFT is an explicit O(M^2) sum, written as a product with the
+    DFT matrix exp(-i*2*pi*((j*k) mod M)/M) built from exact integer indices;
+  * mode="fft": the same sums evaluated with numpy.fft (a library primitive).
+
+Conventions (fs = 1; all axes stored "fftshifted"):
+  * channel k in [-Np/2, Np/2) is stored at kh = k + Np/2   (all Np channels, the
+    down-conversion phase being Np-periodic in k);
+  * FAM second-FFT bin q in [-P/2, P/2) is stored at qh = q + P/2;
+  * SSCA bin q in [-N/2, N/2) is stored at sh = q + N/2;
+  * W_M^j = exp(-i*2*pi*j/M); every phase index is an exact integer product reduced
+    to its non-negative residue mod M before it becomes an angle;
+  * windows g, g_d of the SCD low-pass (Sec. II-A, II-B, II-C) are rectangular (= 1);
+  * no 1/N or 1/P scaling anywhere: raw sums.
+
+Pins (tests/test_oracle_*.py): brute-force triple sums on tiny inputs, direct vs fft
+mode, the averaged-periodogram identity at alpha = 0 (also against scipy's Welch
+estimate), the lag-windowed correlogram at alpha = 0 for SSCA, exact conjugate
+symmetry (FAM), exact channel-shift invariance, |c|^2 scaling, the closed-form FAM
+response to sums of channel-centred tones, cyclic-feature locations of BPSK, and the
+white-noise floor.  The paper prints no worked numeric example, so agreement with the
+paper's own output values is "parity unpinned" (every function here is pinned by the
+identities above instead).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "hamming_window",
+    "twiddle",
+    "fam_demodulates",
+    "fam",
+    "fam_pairs",
+    "ssca_demodulates",
+    "ssca",
+    "fam_map",
+    "ssca_map",
+    "fam_map_coords",
+    "ssca_map_coords",
+]
+
+
+# ----------------------------------------------------------------------------- helpers
+def hamming_window(Np: int) -> np.ndarray:
+    """Symmetric Hamming window a[n] = 0.54 - 0.46 cos(2 pi n / (Np - 1)), rounded to
+    float32 (the window bits both sides consume when the caller passes none)."""
+    n = np.arange(Np, dtype=np.float64)
+    return (0.54 - 0.46 * np.cos(2.0 * np.pi * n / (Np - 1))).astype(np.float32)
+
+
+def twiddle(M: int, idx) -> np.ndarray:
+    """W_M^idx = exp(-i 2 pi idx / M) for integer idx (any sign, any size): the index is
+    reduced exactly to [0, M) as an integer before it is turned into an angle."""
+    j = np.mod(np.asarray(idx, dtype=np.int64), M)
+    return np.exp(-2j * np.pi * (j.astype(np.float64) / M))
+
+
+def _promote(x, a):
+    x = np.asarray(x)
+    a = np.asarray(a)
+    if x.dtype != np.complex64:
+        raise TypeError("x must be complex64 (the bits the GPU path consumes)")
+    if a.dtype != np.float32:
+        raise TypeError("window must be float32 (the bits the GPU path consumes)")
+    return x.astype(np.complex128), a.astype(np.float64)
+
+
+def _signed_channels(Np: int) -> np.ndarray:
+    return np.arange(-Np // 2, Np // 2, dtype=np.int64)
+
+
+def _dft_rows(blocks: np.ndarray, M: int, out_bins: np.ndarray, mode: str) -> np.ndarray:
+    """sum_{j<M} blocks[..., j] W_M^{(j * b) mod M} for each requested bin b."""
+    if mode == "direct":
+        F = twiddle(M, np.outer(np.arange(M, dtype=np.int64), out_bins))
+        return blocks @ F
+    if mode == "fft":
+        return np.fft.fft(blocks, axis=-1)[..., np.mod(out_bins, M)]
+    raise ValueError(f"unknown mode {mode!r}")
+
+
+# ----------------------------------------------------------------------------- FAM
+def fam_demodulates(x, a, Np: int, L: int, P: int, mode: str = "fft") -> np.ndarray:
+    """FAM channeliser (Sec. II-B-1, Eq. II.B-complex_demodulate_final, with the block
+    framing of Algorithm 1 `Framing`: block p covers x[pL .. pL+Np-1]).
+
+        X(p, k) = W_Np^{(k p L) mod Np} * sum_{n<Np} a[n] x[pL + n] W_Np^{(k n) mod Np}
+
+    The first factor is the down-conversion.  Returns complex128 [Np (kh)][P (p)].
+    """
+    x, a = _promote(x, a)
+    if x.shape[0] < (P - 1) * L + Np:
+        raise ValueError("FAM needs N >= (P-1)*L + Np samples")
+    n = np.arange(Np, dtype=np.int64)
+    p = np.arange(P, dtype=np.int64)
+    k = _signed_channels(Np)
+    blocks = x[p[:, None] * L + n[None, :]] * a[None, :]          # [P][Np]
+    spectra = _dft_rows(blocks, Np, k, mode)                      # [P][Np (kh)]
+    down = twiddle(Np, np.outer(p * L, k))                        # W_Np^{k p L}
+    return (spectra * down).T.copy()                              # [kh][p]
+
+
+def _fam_second_fft(z: np.ndarray, P: int, mode: str) -> np.ndarray:
+    """S(q) = sum_{p<P} z(p) W_P^{(q p) mod P} for q in [-P/2, P/2), stored at q + P/2."""
+    q = np.arange(-P // 2, P // 2, dtype=np.int64)
+    return _dft_rows(z, P, q, mode)
+
+
+def fam_pairs(x, a, Np: int, L: int, P: int, kh, lh, mode: str = "fft") -> np.ndarray:
+    """FAM estimate for selected channel pairs (kh[i], lh[i]) (Sec. II-B-2,
+    Eq. II.B-SCD_function_FAM with g_d = 1):
+
+        S(k, l, q) = sum_{p<P} X(p, k) conj(X(p, l)) W_P^{(q p) mod P}
+
+    i.e. the conjugate multiplication followed by the P-point FFT.  Returns complex128
+    [len(kh)][P (qh)].
+    """
+    X = fam_demodulates(x, a, Np, L, P, mode)
+    kh = np.asarray(kh, dtype=np.int64)
+    lh = np.asarray(lh, dtype=np.int64)
+    z = X[kh, :] * np.conj(X[lh, :])                               # [pairs][P]
+    return _fam_second_fft(z, P, mode)
+
+
+def fam(x, a, Np: int, L: int, P: int, mode: str = "fft") -> np.ndarray:
+    """Full FAM estimate, complex128 [Np (kh)][Np (lh)][P (qh)]."""
+    X = fam_demodulates(x, a, Np, L, P, mode)
+    out = np.empty((Np, Np, P), dtype=np.complex128)
+    for kh in range(Np):                                          # one channel row at a time
+        z = X[kh][None, :] * np.conj(X)                           # [lh][p]
+        out[kh] = _fam_second_fft(z, P, mode)
+    return out
+
+
+# ----------------------------------------------------------------------------- SSCA
+def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.ndarray:
+    """SSCA channeliser at hop 1 (Sec. II-C; the complex demodulate of Sec. II-A,
+    Eq. II.A-complex demodulate, centred on sample n, with the window spanning
+    x[n - Np/2 .. n + Np/2 - 1] and x taken as zero outside [0, N)):
+
+        X_T(n, k) = W_Np^{(k s) mod Np} * sum_{r<Np} a[r] x[s + r] W_Np^{(k r) mod Np},
+        s = n - Np/2.
+
+    Returns complex128 [len(n)][len(channels)] (channels are stored indices kh).
+    """
+    x, a = _promote(x, a)
+    N = x.shape[0]
+    n = np.asarray(n, dtype=np.int64)
+    kh = np.arange(Np, dtype=np.int64) if channels is None else np.asarray(channels, np.int64)
+    k = kh - Np // 2
+    s = n - Np // 2
+    m = s[:, None] + np.arange(Np, dtype=np.int64)[None, :]       # absolute sample index
+    inside = (m >= 0) & (m < N)
+    blocks = np.where(inside, x[np.clip(m, 0, N - 1)], 0.0) * a[None, :]
+    spectra = _dft_rows(blocks, Np, k, mode)                      # [n][ch]
+    down = twiddle(Np, np.outer(s, k))                            # W_Np^{k s}
+    return spectra * down
+
+
+def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13) -> np.ndarray:
+    """SSCA estimate (Sec. II-C, Eq. Xg and Eq. II.B-SSCA_auto, with g = 1 and the
+    time origin at the first sample):
+
+        X_g(n, k) = X_T(n, k) conj(x[n])
+        S(k, q)   = sum_{n<N} X_g(n, k) W_N^{(q n) mod N},   q in [-N/2, N/2)
+
+    alpha = k/Np + q/N and f = (k/Np - q/N)/2.  Returns complex128
+    [len(channels)][N (sh)], sh = q + N/2.
+    """
+    xc = np.asarray(x)
+    N = xc.shape[0]
+    kh = np.arange(Np, dtype=np.int64) if channels is None else np.asarray(channels, np.int64)
+    conj_x = np.conj(xc.astype(np.complex128))
+    Xg = np.empty((kh.shape[0], N), dtype=np.complex128)          # channel-major CDP
+    for n0 in range(0, N, chunk):                                 # channeliser in chunks of time
+        n = np.arange(n0, min(N, n0 + chunk), dtype=np.int64)
+        XT = ssca_demodulates(xc, a, Np, n, kh, mode)             # [n][ch]
+        Xg[:, n0:n0 + n.shape[0]] = (XT * conj_x[n][:, None]).T
+    q = np.arange(-N // 2, N // 2, dtype=np.int64)
+    if mode == "direct":
+        if N > 4096:
+            raise ValueError("direct SSCA strip DFT is limited to N <= 4096")
+        return Xg @ twiddle(N, np.outer(np.arange(N, dtype=np.int64), q))
+    out = np.empty_like(Xg)
+    for i in range(kh.shape[0]):
+        out[i] = np.fft.fft(Xg[i])[np.mod(q, N)]
+    return out
+
+
+# ----------------------------------------------------------------------------- maps
+def fam_map_coords(Np: int, L: int, P: int):
+    """Kept FAM cells and their (f, alpha) grid positions.
+
+    Algorithm 1 (`FFT2`) keeps only the central half of each P-point output.  Here the
+    kept band is q in [-Q, Q) with Q = P*L/Np, which equals [-P/4, P/4) when L = Np/4.
+    f = (f_k + f_l)/2 and alpha = f_k - f_l + q/(P L) (Sec. II-B-2), so with integer
+    grid indices fh = k + l + Np (f = (fh - Np)/(2 Np)) and
+    ah = (k - l) Q + q + P L (alpha = (ah - P L)/(P L)).
+    Returns int64 arrays kh, lh, qh, fh, ah (one entry per kept cell).
+    """
+    if (P * L) % Np or 2 * L > Np:
+        raise ValueError("FAM map needs P*L divisible by Np and L <= Np/2")
+    Q = P * L // Np
+    k = _signed_channels(Np)
+    kk, ll, qq = np.meshgrid(k, k, np.arange(-Q, Q, dtype=np.int64), indexing="ij")
+    kk, ll, qq = kk.ravel(), ll.ravel(), qq.ravel()
+    return (kk + Np // 2, ll + Np // 2, qq + P // 2, kk + ll + Np, (kk - ll) * Q + qq + P * L)
+
+
+def fam_map(S: np.ndarray, Np: int, L: int, P: int, power: int = 1) -> np.ndarray:
+    """Scatter |S|^power of the kept FAM cells onto the float64 [2 Np][2 P L] grid;
+    cells that no (k, l, q) reaches stay 0."""
+    kh, lh, qh, fh, ah = fam_map_coords(Np, L, P)
+    grid = np.zeros((2 * Np, 2 * P * L), dtype=np.float64)
+    grid[fh, ah] = np.abs(S[kh, lh, qh]) ** power
+    return grid
+
+
+def ssca_map_coords(N: int, Np: int):
+    """SSCA (f, alpha) positions of every output cell (Sec. II-C: alpha = f_k + q/N,
+    f = (f_k - q/N)/2; the same mapping as Sec. III-B-1's SSCA_2DFFT formula with
+    the stored index M1 m2' + m1' = q + N/2).
+
+    ah = k N/Np + q + N             (alpha = (ah - N)/N, in [-1, 1))
+    fh = floor((k N/Np - q + N) / (2 N/Np))   (f in [fh, fh+1) * 1/Np - 1/2)
+    Returns int64 arrays kh, sh, fh, ah for all Np*N cells.
+    """
+    k = _signed_channels(Np)
+    q = np.arange(-N // 2, N // 2, dtype=np.int64)
+    kk, qq = np.meshgrid(k, q, indexing="ij")
+    kk, qq = kk.ravel(), qq.ravel()
+    D = N // Np
+    ah = kk * D + qq + N
+    fh = np.floor_divide(kk * D - qq + N, 2 * D)
+    return kk + Np // 2, qq + N // 2, fh, ah
+
+
+def ssca_map(S: np.ndarray, N: int, Np: int, power: int = 1) -> np.ndarray:
+    """Scatter |S|^power onto the float64 [Np][2N] grid; unreached cells stay 0."""
+    kh, sh, fh, ah = ssca_map_coords(N, Np)
+    grid = np.zeros((Np, 2 * N), dtype=np.float64)
+    grid[fh, ah] = np.abs(S[kh, sh]) ** power
+    return grid
