@@ -1,0 +1,174 @@
+/* scd.h -- C ABI of libscd.so: spectral correlation density (SCD) estimation on one
+ * NVIDIA GB300 (sm_103a) by the FFT accumulation method (FAM) and the strip spectral
+ * correlation analyser (SSCA), after Li, Wu and Leong, "AMD Versal Implementations of FAM
+ * and SSCA Estimators" (arXiv 2506.18003).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Sample rate fs = 1.  Complex values are complex64: interleaved (re, im) float32 pairs.
+ *  - Channel k in [-Np/2, Np/2) (centre frequency k/Np) is stored at kh = k + Np/2.
+ *    FAM bin q in [-P/2, P/2) is stored at qh = q + P/2; SSCA bin q in [-N/2, N/2) at
+ *    sh = q + N/2 ("fftshifted" axes).
+ *  - W_M^j = exp(-i 2 pi j / M).  Phase indices are exact integer products reduced mod M;
+ *    all phase and twiddle tables are built once in FP64 and rounded.
+ *  - No 1/N or 1/P normalisation (raw sums).  The SCD low-pass windows g and g_d of
+ *    Sec. II are rectangular.
+ *  - Pointers: every data pointer is a DEVICE pointer of the current CUDA device, aligned
+ *    to 16 bytes (8 bytes for float arrays), unless an entry point says otherwise.  The
+ *    caller owns all of them; the library never frees or retains them after the call.
+ *    The library owns only its cached phase tables (released by scd_release_cache()).
+ *  - Asynchrony: work is enqueued on opts->stream (a cudaStream_t; NULL = legacy default
+ *    stream) and the call returns after enqueueing.  Argument errors are returned
+ *    synchronously and enqueue nothing.  SCD_ERR_CUDA means a CUDA launch or runtime
+ *    error; scd_last_error() gives its text.
+ *  - First use of a size builds cached tables (device allocation plus a synchronisation);
+ *    make that first call, or scd_prepare(), outside any stream capture.
+ *  - window == NULL selects the symmetric Hamming window a[n] = 0.54 - 0.46 cos(2 pi n /
+ *    (Np - 1)), computed in FP64 and rounded to float32.
+ */
+#ifndef SCD_H_
+#define SCD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SCD_API __attribute__((visibility("default")))
+#else
+#define SCD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SCD_OK = 0,
+  SCD_ERR_ARG = 1,          /* invalid argument (NULL pointer, bad size, misalignment) */
+  SCD_ERR_UNSUPPORTED = 2,  /* valid but outside the supported sizes */
+  SCD_ERR_CUDA = 3,         /* CUDA runtime or launch error */
+  SCD_ERR_WORKSPACE = 4,    /* workspace missing or smaller than the query */
+  SCD_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired (batched runs) */
+  SCD_ERR_INTERNAL = 6
+} scd_status;
+
+typedef enum { SCD_FP32 = 0, SCD_SPLIT_BF16 = 1 } scd_precision;
+
+/* Options.  Pass NULL for defaults: legacy default stream, FP32, no workspace, |S|,
+ * no stage events.  Zero-initialise the struct before filling it. */
+typedef struct {
+  void* stream;             /* cudaStream_t to enqueue on */
+  int32_t precision;        /* scd_precision */
+  int32_t map_power;        /* maps only: 1 -> |S|, 2 -> |S|^2 */
+  void* workspace;          /* device scratch owned by the caller (may be NULL if 0 needed) */
+  size_t workspace_bytes;   /* its size */
+  /* Optional per-kernel timing: when stage_events is non-NULL and n_stage_events is at
+   * least (kernels launched by the call) + 1, event i (a cudaEvent_t, see
+   * scd_events_create) is recorded on the stream just before the call's i-th kernel and
+   * the next one after its last kernel.  scd_fam launches 2 kernels (channeliser, pair
+   * FFT), scd_ssca 3 (channeliser + CDP, column pass, row pass), each map 1. */
+  void** stage_events;
+  int32_t n_stage_events;
+} scd_opts;
+
+/* ------------------------------------------------------------------------------ FAM
+ * scd_fam: FFT accumulation method, Sec. II-B (Eq. II.B-complex_demodulate_final and
+ * Eq. II.B-SCD_function_FAM), framing as in Algorithm 1 (block p = x[pL .. pL+Np-1]):
+ *   X(p,k)   = W_Np^{(k p L) mod Np} * sum_{n<Np} a[n] x[pL+n] W_Np^{(k n) mod Np}
+ *   S(k,l,q) = sum_{p<P} X(p,k) conj(X(p,l)) W_P^{(q p) mod P}
+ * alpha = (k - l)/Np + q/(P L), f = (k + l)/(2 Np).
+ *   x       complex64[N], N >= (P-1) L + Np (later samples are ignored)
+ *   Np      channels, power of two in [16, 256] (the paper's range 2^4..2^8)
+ *   L       hop between blocks, 1 <= L
+ *   P       blocks, power of two in [2, 16384]
+ *   window  float32[Np] or NULL (Hamming)
+ *   out     complex64[Np][Np][P], out[kh][lh][qh] = S(k, l, q)
+ *   opts    workspace >= scd_fam_workspace_bytes(...) bytes
+ * Errors: SCD_ERR_ARG (NULL/misaligned pointers, N too short, L < 1),
+ *         SCD_ERR_UNSUPPORTED (Np or P out of range / not a power of two, precision),
+ *         SCD_ERR_WORKSPACE, SCD_ERR_CUDA. */
+SCD_API scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window,
+                   void* out, const scd_opts* opts);
+SCD_API size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t P, int32_t precision);
+
+/* ------------------------------------------------------------------------------ SSCA
+ * scd_ssca: strip spectral correlation analyser, Sec. II-C (Eq. Xg and
+ * Eq. II.B-SSCA_auto) with the hop-1 complex demodulate of Sec. II-A
+ * (Eq. II.A-complex demodulate) centred on n, x taken as 0 outside [0, N):
+ *   X_T(n,k) = W_Np^{(k s) mod Np} sum_{r<Np} a[r] x[s+r] W_Np^{(k r) mod Np},  s = n - Np/2
+ *   X_g(n,k) = X_T(n,k) conj(x[n])
+ *   S(k,q)   = sum_{n<N} X_g(n,k) W_N^{(q n) mod N}
+ * alpha = k/Np + q/N, f = (k/Np - q/N)/2.  The N-point transform is the decomposed
+ * (four-step) FFT of Sec. III-B-1 (Eq. Chap4_2DFFT) with N = M1 M2.
+ *   x       complex64[N], N a power of two in [2^12, 2^20] (Sec. III-B-2's range)
+ *   Np      power of two in [16, 256]
+ *   window  float32[Np] or NULL (Hamming)
+ *   out     complex64[Np][N], out[kh][sh] = S(k, q)
+ *   opts    workspace >= scd_ssca_workspace_bytes(...) bytes
+ * Errors as scd_fam. */
+SCD_API scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, void* out,
+                    const scd_opts* opts);
+SCD_API size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision);
+
+/* ------------------------------------------------------------------------------ maps
+ * scd_fam_map: places |S|^map_power of the kept FAM cells on the (f, alpha) grid.
+ * Algorithm 1 (`FFT2`) keeps only the central half of every P-point output; the kept band
+ * is q in [-Q, Q), Q = P L / Np (= [-P/4, P/4) at L = Np/4).  Cell (k, l, q) goes to
+ *   fh = k + l + Np            (f = (fh - Np)/(2 Np))
+ *   ah = (k - l) Q + q + P L   (alpha = (ah - P L)/(P L))
+ * No two cells share a grid point; grid points no cell reaches are written as 0.
+ *   S    complex64[Np][Np][P] (scd_fam's output)
+ *   map  float32[2 Np][2 P L], fully overwritten
+ * Needs P L divisible by Np and 2 L <= Np (else SCD_ERR_UNSUPPORTED). */
+SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts);
+
+/* scd_ssca_map: places |S|^map_power of every SSCA cell on the (f, alpha) grid
+ * (Sec. II-C; Sec. III-B-1's SSCA_2DFFT mapping with stored index M1 m2' + m1' = sh):
+ *   ah = k N/Np + q + N                          (alpha = (ah - N)/N)
+ *   fh = floor((k N/Np - q + N) / (2 N / Np))     (f = fh/Np - 1/2, bin width 1/Np)
+ *   S    complex64[Np][N] (scd_ssca's output)
+ *   map  float32[Np][2 N], fully overwritten (unreached points are 0) */
+SCD_API scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts);
+
+/* ------------------------------------------------------------------------------ host buffers
+ * scd_fam_host / scd_ssca_host: the same estimates for HOST input and output buffers
+ * (pinned memory gives full copy bandwidth; pageable memory works).  The call copies x
+ * (and the window, if given) to the device, runs the estimator, copies the estimate
+ * back and returns only when out_host holds it (the stream is synchronised).  The
+ * device staging area is the caller's workspace: opts->workspace must be a device buffer
+ * of at least scd_*_host_workspace_bytes(...) bytes.  Window, x and out are host
+ * pointers here; errors as for the device entry points. */
+SCD_API scd_status scd_fam_host(const void* x_host, int64_t N, int32_t Np, int32_t L, int32_t P,
+                                const float* window_host, void* out_host, const scd_opts* opts);
+SCD_API size_t scd_fam_host_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t P, int32_t precision);
+SCD_API scd_status scd_ssca_host(const void* x_host, int64_t N, int32_t Np, const float* window_host,
+                                 void* out_host, const scd_opts* opts);
+SCD_API size_t scd_ssca_host_workspace_bytes(int64_t N, int32_t Np, int32_t precision);
+
+/* ------------------------------------------------------------------------------ timing
+ * Helpers for opts->stage_events: create / destroy n CUDA events (with timing) on the
+ * current device, and read the time between two recorded events (blocks until `end`
+ * has completed). */
+SCD_API scd_status scd_events_create(int32_t n, void** events);
+SCD_API scd_status scd_events_destroy(int32_t n, void** events);
+SCD_API scd_status scd_event_elapsed_ms(void* start, void* end, float* ms);
+/* Number of kernels this library has launched in this process (all devices). */
+SCD_API uint64_t scd_launch_count(void);
+
+/* ------------------------------------------------------------------------------ misc */
+/* Builds the cached tables the given sizes need (estimator 0 = FAM with (Np, P), 1 =
+ * SSCA with (Np, N)), so that later calls may be captured in a CUDA graph. */
+SCD_API scd_status scd_prepare(int32_t estimator, int64_t N, int32_t Np, int32_t P);
+/* Frees every cached table on every device (no call may be in flight). */
+SCD_API void scd_release_cache(void);
+SCD_API const char* scd_status_string(scd_status s);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+SCD_API const char* scd_last_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+SCD_API int32_t scd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCD_H_ */

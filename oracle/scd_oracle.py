@@ -43,6 +43,8 @@ __all__ = [
     "fam",
     "fam_pairs",
     "ssca_demodulates",
+    "ssca_cdp",
+    "ssca_strip",
     "ssca",
     "fam_map",
     "ssca_map",
@@ -168,6 +170,27 @@ def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.n
     return spectra * down
 
 
+def ssca_cdp(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.ndarray:
+    """Channel-data product of Sec. II-C, Eq. Xg with g = 1:
+    X_g(n, k) = X_T(n, k) conj(x[n]).  Returns complex128 [len(channels)][len(n)]."""
+    n = np.asarray(n, dtype=np.int64)
+    XT = ssca_demodulates(x, a, Np, n, channels, mode)            # [n][ch]
+    conj_x = np.conj(np.asarray(x).astype(np.complex128)[n])
+    return (XT * conj_x[:, None]).T
+
+
+def ssca_strip(Xg_row: np.ndarray, mode: str = "fft") -> np.ndarray:
+    """N-point strip transform of one channel (Eq. II.B-SSCA_auto, time origin at the first
+    sample): S(q) = sum_{n<N} X_g(n) W_N^{(q n) mod N}, q in [-N/2, N/2) stored at q + N/2."""
+    N = Xg_row.shape[-1]
+    q = np.arange(-N // 2, N // 2, dtype=np.int64)
+    if mode == "direct":
+        if N > 4096:
+            raise ValueError("direct SSCA strip DFT is limited to N <= 4096")
+        return Xg_row @ twiddle(N, np.outer(np.arange(N, dtype=np.int64), q))
+    return np.fft.fft(Xg_row, axis=-1)[..., np.mod(q, N)]
+
+
 def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13) -> np.ndarray:
     """SSCA estimate (Sec. II-C, Eq. Xg and Eq. II.B-SSCA_auto, with g = 1 and the
     time origin at the first sample):
@@ -178,23 +201,17 @@ def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13) 
     alpha = k/Np + q/N and f = (k/Np - q/N)/2.  Returns complex128
     [len(channels)][N (sh)], sh = q + N/2.
     """
-    xc = np.asarray(x)
-    N = xc.shape[0]
+    N = np.asarray(x).shape[0]
     kh = np.arange(Np, dtype=np.int64) if channels is None else np.asarray(channels, np.int64)
-    conj_x = np.conj(xc.astype(np.complex128))
     Xg = np.empty((kh.shape[0], N), dtype=np.complex128)          # channel-major CDP
     for n0 in range(0, N, chunk):                                 # channeliser in chunks of time
         n = np.arange(n0, min(N, n0 + chunk), dtype=np.int64)
-        XT = ssca_demodulates(xc, a, Np, n, kh, mode)             # [n][ch]
-        Xg[:, n0:n0 + n.shape[0]] = (XT * conj_x[n][:, None]).T
-    q = np.arange(-N // 2, N // 2, dtype=np.int64)
+        Xg[:, n0:n0 + n.shape[0]] = ssca_cdp(x, a, Np, n, kh, mode)
     if mode == "direct":
-        if N > 4096:
-            raise ValueError("direct SSCA strip DFT is limited to N <= 4096")
-        return Xg @ twiddle(N, np.outer(np.arange(N, dtype=np.int64), q))
+        return ssca_strip(Xg, mode)                               # one DFT-matrix product
     out = np.empty_like(Xg)
-    for i in range(kh.shape[0]):
-        out[i] = np.fft.fft(Xg[i])[np.mod(q, N)]
+    for i in range(kh.shape[0]):                                  # one channel row at a time
+        out[i] = ssca_strip(Xg[i], mode)
     return out
 
 

@@ -1,0 +1,201 @@
+"""Thin Python binding of libscd.so (include/scd.h): ctypes declarations plus torch-tensor
+marshalling under the same names as the C entry points.
+
+Argument marshalling only: every step of every estimator runs in the library's CUDA
+kernels.  There is no CPU fallback; if the library is missing or cannot be loaded the
+call raises.  PyTorch supplies device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libscd.so")
+
+SCD_OK, SCD_ERR_ARG, SCD_ERR_UNSUPPORTED, SCD_ERR_CUDA, SCD_ERR_WORKSPACE, SCD_ERR_TIMEOUT, SCD_ERR_INTERNAL = range(7)
+SCD_FP32, SCD_SPLIT_BF16 = 0, 1
+PRECISIONS = {"fp32": SCD_FP32, "split": SCD_SPLIT_BF16, "split_bf16": SCD_SPLIT_BF16}
+
+
+class ScdOpts(ctypes.Structure):
+    _fields_ = [
+        ("stream", ctypes.c_void_p),
+        ("precision", ctypes.c_int32),
+        ("map_power", ctypes.c_int32),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
+        ("n_stage_events", ctypes.c_int32),
+    ]
+
+
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_opts_p = ctypes.POINTER(ScdOpts)
+
+# name -> (restype, argtypes); every function include/scd.h declares
+SIGNATURES = {
+    "scd_fam": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _opts_p]),
+    "scd_fam_workspace_bytes": (_sz, [_i64, _i32, _i32, _i32, _i32]),
+    "scd_ssca": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p]),
+    "scd_ssca_workspace_bytes": (_sz, [_i64, _i32, _i32]),
+    "scd_fam_map": (_i32, [_vp, _i32, _i32, _i32, _vp, _opts_p]),
+    "scd_ssca_map": (_i32, [_vp, _i64, _i32, _vp, _opts_p]),
+    "scd_fam_host": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _opts_p]),
+    "scd_fam_host_workspace_bytes": (_sz, [_i64, _i32, _i32, _i32, _i32]),
+    "scd_ssca_host": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p]),
+    "scd_ssca_host_workspace_bytes": (_sz, [_i64, _i32, _i32]),
+    "scd_events_create": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
+    "scd_events_destroy": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
+    "scd_event_elapsed_ms": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "scd_launch_count": (ctypes.c_uint64, []),
+    "scd_prepare": (_i32, [_i32, _i64, _i32, _i32]),
+    "scd_release_cache": (None, []),
+    "scd_status_string": (ctypes.c_char_p, [_i32]),
+    "scd_last_error": (ctypes.c_char_p, []),
+    "scd_version": (_i32, []),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libscd.so (built in-tree by build.py) and declares its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libscd.so not found at {p}: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class ScdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.scd_status_string(status).decode()
+        if status == SCD_ERR_CUDA:
+            msg += f" ({lib.scd_last_error().decode()})"
+        super().__init__(f"{where}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != SCD_OK:
+        raise ScdError(status, where)
+
+
+# ----------------------------------------------------------------------------- torch layer
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, numel, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor of at least {numel} elements")
+
+
+def make_opts(stream=None, precision="fp32", workspace=None, map_power=1) -> ScdOpts:
+    o = ScdOpts()
+    o.stream = _stream(stream)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.map_power = int(map_power)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def _workspace(nbytes, device, workspace):
+    torch = _torch()
+    if workspace is not None:
+        return workspace
+    return torch.empty(max(1, nbytes), dtype=torch.uint8, device=device)
+
+
+def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32", stream=None, workspace=None):
+    """FAM estimate of the complex64 CUDA tensor x; returns complex64 [Np, Np, P]."""
+    torch = _torch()
+    lib = load()
+    _need(x, torch.complex64, 1, "x")
+    N = x.numel()
+    if window is not None:
+        _need(window, torch.float32, Np, "window")
+    if out is None:
+        out = torch.empty((Np, Np, P), dtype=torch.complex64, device=x.device)
+    _need(out, torch.complex64, Np * Np * P, "out")
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    ws = _workspace(lib.scd_fam_workspace_bytes(N, Np, L, P, prec), x.device, workspace)
+    o = make_opts(stream, prec, ws)
+    check(lib.scd_fam(_ptr(x), N, Np, L, P, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_fam")
+    return out
+
+
+def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None):
+    """SSCA estimate of the complex64 CUDA tensor x (N = x.numel()); returns complex64 [Np, N]."""
+    torch = _torch()
+    lib = load()
+    _need(x, torch.complex64, 1, "x")
+    N = x.numel()
+    if window is not None:
+        _need(window, torch.float32, Np, "window")
+    if out is None:
+        out = torch.empty((Np, N), dtype=torch.complex64, device=x.device)
+    _need(out, torch.complex64, Np * N, "out")
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    ws = _workspace(lib.scd_ssca_workspace_bytes(N, Np, prec), x.device, workspace)
+    o = make_opts(stream, prec, ws)
+    check(lib.scd_ssca(_ptr(x), N, Np, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_ssca")
+    return out
+
+
+def scd_fam_map(S, Np: int, L: int, P: int, map=None, power: int = 1, stream=None):
+    """(f, alpha) grid float32 [2 Np, 2 P L] of a FAM estimate S."""
+    torch = _torch()
+    lib = load()
+    _need(S, torch.complex64, Np * Np * P, "S")
+    if map is None:
+        map = torch.empty((2 * Np, 2 * P * L), dtype=torch.float32, device=S.device)
+    _need(map, torch.float32, 4 * Np * P * L, "map")
+    o = make_opts(stream, "fp32", None, power)
+    check(lib.scd_fam_map(_ptr(S), Np, L, P, _ptr(map), ctypes.byref(o)), "scd_fam_map")
+    return map
+
+
+def scd_ssca_map(S, N: int, Np: int, map=None, power: int = 1, stream=None):
+    """(f, alpha) grid float32 [Np, 2 N] of an SSCA estimate S."""
+    torch = _torch()
+    lib = load()
+    _need(S, torch.complex64, Np * N, "S")
+    if map is None:
+        map = torch.empty((Np, 2 * N), dtype=torch.float32, device=S.device)
+    _need(map, torch.float32, 2 * Np * N, "map")
+    o = make_opts(stream, "fp32", None, power)
+    check(lib.scd_ssca_map(_ptr(S), N, Np, _ptr(map), ctypes.byref(o)), "scd_ssca_map")
+    return map
+
+
+def scd_prepare(estimator: str, N: int, Np: int, P: int = 2) -> None:
+    lib = load()
+    check(lib.scd_prepare({"fam": 0, "ssca": 1}[estimator], N, Np, P), "scd_prepare")

@@ -1,0 +1,274 @@
+// Batched power-of-two FFT building blocks for the SCD kernels (sm_103a).
+//
+// Every DFT on the hot path is a forward transform, X[f] = sum_n x[n] W_M^{f n} with
+// W_M = exp(-i 2 pi / M).  A size-M transform is carried by a team of T threads that each
+// hold E = M/T complex values in registers.  It runs as a short sequence of Stockham
+// radix-R passes (R in {2..32}); the first pass reads straight from the producer (global
+// memory or an on-the-fly product), the last pass hands each output straight to the
+// consumer, and only the passes in between go through shared memory.
+//
+// Stockham recurrence used by every pass (decimation in time).  With p the product of the
+// radices already applied, the array holds A_p[s, k] = sum_{t<p} x[s + t M/p] W_p^{k t} at
+// index k + s p.  One radix-R pass turns A_p into A_{pR}:
+//     A_{pR}[s, k + p j] = sum_{r<R} W_R^{j r} ( W_{pR}^{k r} A_p[s + r M/(pR), k] ),
+// so butterfly i = k + s p (i < M/R) reads indices i + r M/R, scales them by W_{pR}^{k r},
+// runs an R-point DFT and writes output j to index (i - k) R + k + p j.  After the last
+// pass (pR = M) the output index is the natural frequency index.
+//
+// Twiddles W_{pR}^{k r} come from per-size tables built once in FP64 from exact integer
+// indices (tables.cu); the radix-R butterflies use compile-time constants.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace scd {
+
+// ----------------------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ----------------------------------------------------------------------------- radix plans
+// Radices of the Stockham passes for a size-M transform; the largest radix comes first,
+// so p jumps from 1 straight to >= 8 and the shared-memory writes stay bank-friendly.
+template <int M> struct Plan;
+template <> struct Plan<2>     { static constexpr int n = 1; static constexpr int r[3] = {2, 0, 0}; };
+template <> struct Plan<4>     { static constexpr int n = 1; static constexpr int r[3] = {4, 0, 0}; };
+template <> struct Plan<8>     { static constexpr int n = 1; static constexpr int r[3] = {8, 0, 0}; };
+template <> struct Plan<16>    { static constexpr int n = 1; static constexpr int r[3] = {16, 0, 0}; };
+template <> struct Plan<32>    { static constexpr int n = 1; static constexpr int r[3] = {32, 0, 0}; };
+template <> struct Plan<64>    { static constexpr int n = 2; static constexpr int r[3] = {8, 8, 0}; };
+template <> struct Plan<128>   { static constexpr int n = 2; static constexpr int r[3] = {16, 8, 0}; };
+template <> struct Plan<256>   { static constexpr int n = 2; static constexpr int r[3] = {16, 16, 0}; };
+template <> struct Plan<512>   { static constexpr int n = 2; static constexpr int r[3] = {32, 16, 0}; };
+template <> struct Plan<1024>  { static constexpr int n = 2; static constexpr int r[3] = {32, 32, 0}; };
+template <> struct Plan<2048>  { static constexpr int n = 3; static constexpr int r[3] = {16, 16, 8}; };
+template <> struct Plan<4096>  { static constexpr int n = 3; static constexpr int r[3] = {16, 16, 16}; };
+template <> struct Plan<8192>  { static constexpr int n = 3; static constexpr int r[3] = {32, 16, 16}; };
+template <> struct Plan<16384> { static constexpr int n = 3; static constexpr int r[3] = {32, 32, 16}; };
+
+template <int M> struct PlanInfo {
+  static constexpr int n = Plan<M>::n;
+  static constexpr int r0 = Plan<M>::r[0], r1 = Plan<M>::r[1], r2 = Plan<M>::r[2];
+  static constexpr int E = r0;            // values per thread (largest radix first)
+  static constexpr int T = M / E;         // threads per transform
+  // product of radices before pass s
+  static constexpr int p(int s) { return s == 0 ? 1 : (s == 1 ? r0 : r0 * r1); }
+  static constexpr int R(int s) { return s == 0 ? r0 : (s == 1 ? r1 : r2); }
+  // offset of pass s (s >= 1) in the concatenated pass-twiddle table; entry (r, k) of pass
+  // s sits at off(s) + r p(s) + k and holds W_{p R}^{k r}
+  static constexpr int off(int s) { return s <= 1 ? 0 : r0 * r1; }
+  static constexpr int tw_len() { return n == 1 ? 1 : (n == 2 ? r0 * r1 : r0 * r1 + r0 * r1 * r2); }
+  // shared-memory stride (complex elements) of one transform: one pad element per 16 and a
+  // stride of 1 mod 16 so that transforms laid side by side fall in different banks
+  static constexpr int stride() { return M + M / 16 + 1; }
+};
+
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+
+// ----------------------------------------------------------------------------- radix-R DFT
+// W_32^j for j < 16 (cos, -sin), double literals rounded to float at compile time.
+struct W32 {
+  static constexpr float c[16] = {1.0f, 0.99518472667219693f, 0.98078528040323043f, 0.95694033573220882f,
+                                  0.92387953251128674f, 0.88192126434835505f, 0.83146961230254524f,
+                                  0.77301045336273699f, 0.70710678118654757f, 0.63439328416364549f,
+                                  0.55557023301960229f, 0.47139673682599781f, 0.38268343236508984f,
+                                  0.29028467725446233f, 0.19509032201612833f, 0.09801714032956077f};
+  static constexpr float s[16] = {0.0f, -0.098017140329560604f, -0.19509032201612825f, -0.29028467725446233f,
+                                  -0.38268343236508978f, -0.47139673682599764f, -0.55557023301960218f,
+                                  -0.63439328416364549f, -0.70710678118654746f, -0.77301045336273699f,
+                                  -0.83146961230254524f, -0.88192126434835494f, -0.92387953251128674f,
+                                  -0.95694033573220894f, -0.98078528040323043f, -0.99518472667219682f};
+};
+
+// d * W_{L}^{j}, L <= 32, with the trivial factors (1, -i, (+-1 - i)/sqrt2) special-cased
+template <int L, int J>
+__device__ __forceinline__ float2 twc(float2 d) {
+  constexpr int q = J * (32 / L);          // W_L^J = W_32^q, q < 16
+  if constexpr (q == 0) {
+    return d;
+  } else if constexpr (q == 8) {           // -i
+    return make_float2(d.y, -d.x);
+  } else if constexpr (q == 4) {           // (1 - i)/sqrt2
+    constexpr float h = 0.70710678118654752f;
+    return make_float2((d.x + d.y) * h, (d.y - d.x) * h);
+  } else if constexpr (q == 12) {          // (-1 - i)/sqrt2
+    constexpr float h = 0.70710678118654752f;
+    return make_float2((d.y - d.x) * h, -(d.x + d.y) * h);
+  } else {
+    constexpr float c = W32::c[q], s = W32::s[q];
+    return make_float2(fmaf(d.x, c, -d.y * s), fmaf(d.x, s, d.y * c));
+  }
+}
+
+template <int R, int SPAN, int START, int J>
+__device__ __forceinline__ void dif_bfly(float2* v) {
+  if constexpr (J < SPAN) {
+    float2 a = v[START + J], b = v[START + J + SPAN];
+    v[START + J] = cadd(a, b);
+    v[START + J + SPAN] = twc<2 * SPAN, J>(csub(a, b));
+    dif_bfly<R, SPAN, START, J + 1>(v);
+  }
+}
+template <int R, int SPAN, int START>
+__device__ __forceinline__ void dif_stage(float2* v) {
+  if constexpr (START < R) {
+    dif_bfly<R, SPAN, START, 0>(v);
+    dif_stage<R, SPAN, START + 2 * SPAN>(v);
+  }
+}
+template <int R, int SPAN>
+__device__ __forceinline__ void dif_all(float2* v) {
+  if constexpr (SPAN >= 1) {
+    dif_stage<R, SPAN, 0>(v);
+    dif_all<R, SPAN / 2>(v);
+  }
+}
+__host__ __device__ constexpr int bitrev(int i, int R) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) { r = (r << 1) | (i & 1); i >>= 1; }
+  return r;
+}
+template <int R, int I>
+__device__ __forceinline__ void unscramble(float2* v) {
+  if constexpr (I < R) {
+    constexpr int J = bitrev(I, R);
+    if constexpr (J > I) { float2 t = v[I]; v[I] = v[J]; v[J] = t; }
+    unscramble<R, I + 1>(v);
+  }
+}
+// In-register R-point forward DFT, natural order in and out (radix-2 DIF network).
+template <int R>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R > 1) {
+    dif_all<R, R / 2>(v);
+    unscramble<R, 0>(v);
+  }
+}
+
+// ----------------------------------------------------------------------------- batched FFT
+// C transforms of size M per CTA, T = M/E threads each (blockDim.x == C*T).
+// CFAST: thread tid works on transform c = tid % C (transforms interleaved across lanes,
+// good when consecutive transforms touch consecutive addresses); otherwise c = tid / T
+// (a transform's threads are consecutive).  `sm` holds C regions of PlanInfo<M>::stride()
+// complex values; `tw` is the concatenated pass-twiddle table for size M.
+//   src(c, idx)      -> float2   input idx of transform c (idx in [0, M))
+//   dst(c, f, value)             output bin f (natural order) of transform c
+// SYNC_DST: put a CTA barrier between the last pass's shared-memory reads and the dst
+// calls, for consumers that stage outputs in the same shared memory.  Callers that loop
+// over several batches must also barrier between batches.
+template <int M, int C, bool CFAST, bool SYNC_DST, class Src, class Dst>
+__device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2* __restrict__ tw,
+                                          Src& src, Dst& dst) {
+  using PI = PlanInfo<M>;
+  constexpr int E = PI::E, T = PI::T;
+  const int tid = threadIdx.x;
+  const int c = CFAST ? (tid % C) : (tid / T);
+  const int t = CFAST ? (tid / C) : (tid % T);
+  float2* reg = sm + c * PI::stride();
+  float2 v[E];
+
+  // ---- pass 0 (p = 1): read from the producer, no twiddles
+  constexpr int R0 = PI::r0;
+  static_assert(E == R0, "first pass must use the largest radix");
+  {
+    const int i = t;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[r] = src(c, i + r * (M / R0));
+    dft<R0>(v);
+  }
+  if constexpr (PI::n == 1) {
+#pragma unroll
+    for (int j = 0; j < R0; ++j) dst(c, j, v[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < R0; ++j) reg[spad(t * R0 + j)] = v[j];
+    __syncthreads();
+    // ---- pass 1
+    constexpr int R1 = PI::r1, p1 = PI::p(1), B1 = E / R1;
+#pragma unroll
+    for (int b = 0; b < B1; ++b) {
+      const int i = t + b * T;
+      const int k = i & (p1 - 1);
+#pragma unroll
+      for (int r = 0; r < R1; ++r) {
+        float2 x = reg[spad(i + r * (M / R1))];
+        if (r > 0) x = cmul(x, __ldg(tw + PI::off(1) + r * p1 + k));
+        v[b * R1 + r] = x;
+      }
+      dft<R1>(v + b * R1);
+    }
+    if constexpr (PI::n == 2) {
+      if constexpr (SYNC_DST) __syncthreads();
+#pragma unroll
+      for (int b = 0; b < B1; ++b) {
+        const int i = t + b * T;
+        const int k = i & (p1 - 1);
+#pragma unroll
+        for (int j = 0; j < R1; ++j) dst(c, (i - k) * R1 + k + p1 * j, v[b * R1 + j]);
+      }
+    } else {
+      __syncthreads();                     // every read of this pass precedes the writes
+#pragma unroll
+      for (int b = 0; b < B1; ++b) {
+        const int i = t + b * T;
+        const int k = i & (p1 - 1);
+#pragma unroll
+        for (int j = 0; j < R1; ++j) reg[spad((i - k) * R1 + k + p1 * j)] = v[b * R1 + j];
+      }
+      __syncthreads();
+      // ---- pass 2
+      constexpr int R2 = PI::r2, p2 = PI::p(2), B2 = E / R2;
+#pragma unroll
+      for (int b = 0; b < B2; ++b) {
+        const int i = t + b * T;
+        const int k = i & (p2 - 1);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+          float2 x = reg[spad(i + r * (M / R2))];
+          if (r > 0) x = cmul(x, __ldg(tw + PI::off(2) + r * p2 + k));
+          v[b * R2 + r] = x;
+        }
+        dft<R2>(v + b * R2);
+      }
+      if constexpr (SYNC_DST) __syncthreads();
+#pragma unroll
+      for (int b = 0; b < B2; ++b) {
+        const int i = t + b * T;
+        const int k = i & (p2 - 1);
+#pragma unroll
+        for (int j = 0; j < R2; ++j) dst(c, (i - k) * R2 + k + p2 * j, v[b * R2 + j]);
+      }
+    }
+  }
+}
+
+// Invokes F::template run<M>() for a runtime power-of-two M in [2, 16384].
+#define SCD_DISPATCH_POW2(M_RUNTIME, CALL)                     \
+  switch (M_RUNTIME) {                                          \
+    case 2: CALL(2); break;                                     \
+    case 4: CALL(4); break;                                     \
+    case 8: CALL(8); break;                                     \
+    case 16: CALL(16); break;                                   \
+    case 32: CALL(32); break;                                   \
+    case 64: CALL(64); break;                                   \
+    case 128: CALL(128); break;                                 \
+    case 256: CALL(256); break;                                 \
+    case 512: CALL(512); break;                                 \
+    case 1024: CALL(1024); break;                               \
+    case 2048: CALL(2048); break;                               \
+    case 4096: CALL(4096); break;                               \
+    case 8192: CALL(8192); break;                               \
+    case 16384: CALL(16384); break;                             \
+    default: return SCD_ERR_UNSUPPORTED;                        \
+  }
+
+}  // namespace scd

@@ -1,0 +1,50 @@
+// Internal interfaces between the C-ABI layer and the kernels (not exported).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/scd.h"
+
+namespace scd {
+
+// ---------------------------------------------------------------- phase tables (tables.cu)
+// Every table is built once per device on first use, in FP64 from exact integer indices,
+// rounded to float2 (and, for the split form, to bf16 hi/lo), and cached until
+// scd_release_cache() or process exit.  The returned pointers are device pointers valid
+// on every stream of that device.  Building allocates device memory and synchronises, so
+// the first call for a size must not happen inside a stream capture.
+const float2* table_roots(int M, cudaError_t* err);        // W_M^j, j in [0, M)
+const float2* table_pass(int M, cudaError_t* err);         // Stockham pass twiddles of a size-M FFT
+const float2* table_cols(int N, int M1, int C, cudaError_t* err);  // W_N^{c m1'}, [m1'][c], c < C
+const float* table_hamming(int Np, cudaError_t* err);      // default window, float32
+void release_tables();
+
+// ---------------------------------------------------------------- FAM (fam.cu)
+// X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL + n] W_Np^{(k n) mod Np}
+cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* window, float2* X,
+                           cudaStream_t st);
+// out[kh][lh][qh] = sum_p X[kh][p] conj(X[lh][p]) W_P^{(q p) mod P}
+cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- SSCA (ssca.cu)
+constexpr int kSscaCols = 8;       // columns m2 per CTA in the column pass
+void ssca_split(int64_t N, int* M1, int* M2);
+// Stage 0: channeliser + CDP, X_g into ws[kh][n]
+cudaError_t ssca_cdp(const float2* x, int64_t N, int Np, const float* window, float2* ws, cudaStream_t st);
+// Stage 1: M1-point column FFTs times the rotate factor, in place on ws
+cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st);
+// Stage 2: M2-point row FFTs, fftshifted into out[kh][sh]
+cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- maps (map.cu)
+cudaError_t fam_map(const float2* S, int Np, int L, int P, int power, float* map, cudaStream_t st);
+cudaError_t ssca_map(const float2* S, int64_t N, int Np, int power, float* map, cudaStream_t st);
+
+// ---------------------------------------------------------------- launch accounting
+void count_launches(int n);
+
+// ---------------------------------------------------------------- helpers
+inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+
+}  // namespace scd

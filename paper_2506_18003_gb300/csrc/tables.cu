@@ -1,0 +1,151 @@
+// K0: FP64 phase and twiddle tables.
+//
+// The down-conversion phases W_Np^{(k p L) mod Np} (Eq. II.B-complex_demodulate_final),
+// W_Np^{(k s) mod Np} (SSCA channeliser), the rotate factor W_N^{(m2 m1') mod N} of the
+// decomposed FFT (Eq. Chap4_2DFFT) and the Stockham pass twiddles are all of the form
+// W_M^j with an exact integer j in [0, M).  Each entry is computed once with FP64
+// sincospi(2 j / M) (argument exact: M is a power of two) and rounded to float32, so no
+// phase ever loses accuracy to an FP32 angle, even at M = 2^20.
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace scd {
+namespace {
+
+__device__ __forceinline__ float2 root_fp64(int64_t j, int64_t M) {
+  double s, c;
+  sincospi(2.0 * (double)j / (double)M, &s, &c);
+  return make_float2((float)c, (float)(-s));
+}
+
+__global__ void k_roots(float2* out, int64_t M) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = root_fp64(j, M);
+}
+
+// Stockham pass twiddles: for pass s (s >= 1) with p = prod of earlier radices and radix R,
+// entry off_s + r p + k = W_{pR}^{k r} = W_M^{k r M/(pR)} (k < p, r < R, so the index is < M).
+__global__ void k_pass(float2* out, int M, int r0, int r1, int r2) {
+  const int n1 = r0 * r1, n2 = r2 ? r0 * r1 * r2 : 0;
+  const int total = n1 + n2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int p, R, loc;
+    if (e < n1) { p = r0; R = r1; loc = e; }
+    else        { p = r0 * r1; R = r2; loc = e - n1; }
+    const int r = loc / p, k = loc % p;
+    const int64_t j = (int64_t)k * r * (M / (p * R));
+    out[e] = root_fp64(j, M);
+  }
+}
+
+// W_N^{c m1'} for c < C, m1' < M1 at [m1'][c] (c m1' < C M1 <= N: no reduction needed)
+__global__ void k_cols(float2* out, int64_t N, int M1, int C) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M1 * C; e += gridDim.x * blockDim.x) {
+    const int m1 = e / C, c = e % C;
+    out[e] = root_fp64(((int64_t)c * m1) % N, N);
+  }
+}
+
+__global__ void k_hamming(float* out, int Np) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < Np) out[n] = (float)(0.54 - 0.46 * cospi(2.0 * (double)n / (double)(Np - 1)));
+}
+
+struct Key {
+  int dev, kind;
+  int64_t a, b, c;
+  bool operator<(const Key& o) const { return std::tie(dev, kind, a, b, c) < std::tie(o.dev, o.kind, o.a, o.b, o.c); }
+};
+
+std::mutex g_mu;
+std::map<Key, void*> g_tables;
+
+struct PassRadices { int r0, r1, r2; };
+PassRadices pass_radices(int M) {
+  PassRadices r{0, 0, 0};
+#define SCD_PR(MM) r = {Plan<MM>::r[0], Plan<MM>::r[1], Plan<MM>::r[2]}
+  switch (M) {
+    case 2: SCD_PR(2); break;       case 4: SCD_PR(4); break;       case 8: SCD_PR(8); break;
+    case 16: SCD_PR(16); break;     case 32: SCD_PR(32); break;     case 64: SCD_PR(64); break;
+    case 128: SCD_PR(128); break;   case 256: SCD_PR(256); break;   case 512: SCD_PR(512); break;
+    case 1024: SCD_PR(1024); break; case 2048: SCD_PR(2048); break; case 4096: SCD_PR(4096); break;
+    case 8192: SCD_PR(8192); break; case 16384: SCD_PR(16384); break;
+    default: break;
+  }
+#undef SCD_PR
+  return r;
+}
+
+// Returns the cached table for key, building it with `build(ptr, stream)` on first use.
+template <class Build>
+void* get_or_build(int kind, int64_t a, int64_t b, int64_t c, size_t bytes, cudaError_t* err, Build build) {
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  Key key{dev, kind, a, b, c};
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_tables.find(key);
+  if (it != g_tables.end()) return it->second;
+  void* ptr = nullptr;
+  if ((*err = cudaMalloc(&ptr, bytes)) != cudaSuccess) return nullptr;
+  cudaStream_t st;
+  if ((*err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) { cudaFree(ptr); return nullptr; }
+  build(ptr, st);
+  *err = cudaGetLastError();
+  if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (*err != cudaSuccess) { cudaFree(ptr); return nullptr; }
+  g_tables[key] = ptr;
+  return ptr;
+}
+
+int grid_for(int64_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
+
+}  // namespace
+
+const float2* table_roots(int M, cudaError_t* err) {
+  return (const float2*)get_or_build(0, M, 0, 0, sizeof(float2) * (size_t)M, err, [&](void* p, cudaStream_t st) {
+    k_roots<<<grid_for(M), 256, 0, st>>>((float2*)p, M);
+  });
+}
+
+const float2* table_pass(int M, cudaError_t* err) {
+  PassRadices r = pass_radices(M);
+  if (r.r0 == 0) { *err = cudaErrorInvalidValue; return nullptr; }
+  int len = r.r1 ? r.r0 * r.r1 + (r.r2 ? r.r0 * r.r1 * r.r2 : 0) : 1;
+  return (const float2*)get_or_build(1, M, 0, 0, sizeof(float2) * (size_t)len, err, [&](void* p, cudaStream_t st) {
+    if (r.r1) k_pass<<<grid_for(len), 256, 0, st>>>((float2*)p, M, r.r0, r.r1, r.r2);
+    else cudaMemsetAsync(p, 0, sizeof(float2), st);
+  });
+}
+
+const float2* table_cols(int N, int M1, int C, cudaError_t* err) {
+  return (const float2*)get_or_build(2, N, M1, C, sizeof(float2) * (size_t)M1 * C, err, [&](void* p, cudaStream_t st) {
+    k_cols<<<grid_for((int64_t)M1 * C), 256, 0, st>>>((float2*)p, N, M1, C);
+  });
+}
+
+const float* table_hamming(int Np, cudaError_t* err) {
+  return (const float*)get_or_build(3, Np, 0, 0, sizeof(float) * (size_t)Np, err, [&](void* p, cudaStream_t st) {
+    k_hamming<<<(Np + 255) / 256, 256, 0, st>>>((float*)p, Np);
+  });
+}
+
+void release_tables() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_tables) {
+    cudaSetDevice(kv.first.dev);
+    cudaFree(kv.second);
+  }
+  cudaSetDevice(cur);
+  g_tables.clear();
+}
+
+}  // namespace scd

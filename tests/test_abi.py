@@ -1,0 +1,104 @@
+"""The C-ABI library loads, exports every symbol include/scd.h declares, and rejects bad
+arguments synchronously (these checks run before any CUDA call, so no GPU is needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_18003_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "scd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(scd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_what_binding_declares():
+    assert declared_functions() == sorted(binding.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_library_hides_internal_symbols():
+    out = os.popen(f"nm -D --defined-only {binding.LIB_PATH}").read()
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    ours = {s for s in exported if s.startswith("scd")}
+    assert ours == set(declared_functions())
+
+
+def test_status_strings(lib):
+    for s in range(7):
+        assert lib.scd_status_string(s)
+    assert lib.scd_version() >= 100
+
+
+def test_workspace_queries(lib):
+    assert lib.scd_fam_workspace_bytes(65728, 256, 64, 1024, 0) == 256 * 1024 * 8
+    assert lib.scd_ssca_workspace_bytes(1 << 20, 256, 0) == 256 * (1 << 20) * 8
+    assert lib.scd_fam_workspace_bytes(280, 32, 8, 32, 0) % 256 == 0
+
+
+FAKE = ctypes.c_void_p(1 << 20)        # aligned, never dereferenced: validation fails first
+
+
+@pytest.mark.parametrize("N,Np,L,P,expect", [
+    (280, 32, 8, 32, None),                            # valid (not run here)
+    (279, 32, 8, 32, binding.SCD_ERR_ARG),             # N < (P-1) L + Np
+    (280, 32, 0, 32, binding.SCD_ERR_ARG),             # L < 1
+    (280, 24, 8, 32, binding.SCD_ERR_UNSUPPORTED),     # Np not a power of two
+    (280, 8, 8, 32, binding.SCD_ERR_UNSUPPORTED),      # Np below 16
+    (4000, 512, 8, 32, binding.SCD_ERR_UNSUPPORTED),   # Np above 256
+    (280, 32, 8, 30, binding.SCD_ERR_UNSUPPORTED),     # P not a power of two
+    (1 << 20, 32, 1, 32768, binding.SCD_ERR_UNSUPPORTED),
+])
+def test_fam_argument_validation(lib, N, Np, L, P, expect):
+    if expect is None:
+        return
+    assert lib.scd_fam(FAKE, N, Np, L, P, None, FAKE, None) == expect
+
+
+def test_null_and_misaligned_pointers(lib):
+    assert lib.scd_fam(None, 280, 32, 8, 32, None, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, None, None) == binding.SCD_ERR_ARG
+    assert lib.scd_fam(ctypes.c_void_p((1 << 20) + 4), 280, 32, 8, 32, None, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, ctypes.c_void_p((1 << 20) + 8), None) == binding.SCD_ERR_ARG
+    assert lib.scd_ssca(None, 4096, 32, None, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_fam_map(None, 32, 8, 32, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_ssca_map(FAKE, 4096, 32, None, None) == binding.SCD_ERR_ARG
+
+
+@pytest.mark.parametrize("N,Np,expect", [
+    (2048, 32, binding.SCD_ERR_UNSUPPORTED),           # below 2^12
+    (1 << 21, 32, binding.SCD_ERR_UNSUPPORTED),        # above 2^20
+    (5000, 32, binding.SCD_ERR_UNSUPPORTED),           # not a power of two
+    (4096, 48, binding.SCD_ERR_UNSUPPORTED),
+])
+def test_ssca_argument_validation(lib, N, Np, expect):
+    assert lib.scd_ssca(FAKE, N, Np, None, FAKE, None) == expect
+
+
+def test_workspace_is_required(lib):
+    o = binding.ScdOpts()
+    o.precision = 0
+    o.map_power = 1
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_WORKSPACE
+    o.workspace = 1 << 20
+    o.workspace_bytes = 16
+    assert lib.scd_ssca(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_WORKSPACE
+
+
+def test_map_validation(lib):
+    o = binding.ScdOpts()
+    o.map_power = 3
+    assert lib.scd_fam_map(FAKE, 32, 8, 32, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    assert lib.scd_fam_map(FAKE, 32, 20, 32, FAKE, None) == binding.SCD_ERR_UNSUPPORTED   # 2L > Np
+    assert lib.scd_fam_map(FAKE, 32, 3, 8, FAKE, None) == binding.SCD_ERR_UNSUPPORTED     # PL % Np
