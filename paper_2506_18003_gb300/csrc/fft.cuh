@@ -24,17 +24,17 @@
 namespace scd {
 
 // ----------------------------------------------------------------------------- complex
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 // a * conj(b)
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
 // ----------------------------------------------------------------------------- radix plans
 // Radices of the Stockham passes for a size-M transform; the largest radix comes first,
@@ -72,26 +72,18 @@ template <int M> struct PlanInfo {
   static constexpr int stride() { return M + M / 16 + 1; }
 };
 
-__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 
 // ----------------------------------------------------------------------------- radix-R DFT
 // W_32^j for j < 16 (cos, -sin), double literals rounded to float at compile time.
 struct W32 {
-  static constexpr float c[16] = {1.0f, 0.99518472667219693f, 0.98078528040323043f, 0.95694033573220882f,
-                                  0.92387953251128674f, 0.88192126434835505f, 0.83146961230254524f,
-                                  0.77301045336273699f, 0.70710678118654757f, 0.63439328416364549f,
-                                  0.55557023301960229f, 0.47139673682599781f, 0.38268343236508984f,
-                                  0.29028467725446233f, 0.19509032201612833f, 0.09801714032956077f};
-  static constexpr float s[16] = {0.0f, -0.098017140329560604f, -0.19509032201612825f, -0.29028467725446233f,
-                                  -0.38268343236508978f, -0.47139673682599764f, -0.55557023301960218f,
-                                  -0.63439328416364549f, -0.70710678118654746f, -0.77301045336273699f,
-                                  -0.83146961230254524f, -0.88192126434835494f, -0.92387953251128674f,
-                                  -0.95694033573220894f, -0.98078528040323043f, -0.99518472667219682f};
+  static constexpr float c[16] = {1.0f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f, 0.70710678118654757f, 0.55557023301960229f, 0.38268343236508984f, 0.19509032201612833f, 0.0f, -0.19509032201612819f, -0.38268343236508973f, -0.55557023301960196f, -0.70710678118654746f, -0.83146961230254535f, -0.92387953251128674f, -0.98078528040323043f};
+  static constexpr float s[16] = {0.0f, -0.19509032201612825f, -0.38268343236508978f, -0.55557023301960218f, -0.70710678118654746f, -0.83146961230254524f, -0.92387953251128674f, -0.98078528040323043f, -1.0f, -0.98078528040323043f, -0.92387953251128674f, -0.83146961230254546f, -0.70710678118654757f, -0.55557023301960218f, -0.38268343236508989f, -0.19509032201612861f};
 };
 
 // d * W_{L}^{j}, L <= 32, with the trivial factors (1, -i, (+-1 - i)/sqrt2) special-cased
 template <int L, int J>
-__device__ __forceinline__ float2 twc(float2 d) {
+__host__ __device__ __forceinline__ float2 twc(float2 d) {
   constexpr int q = J * (32 / L);          // W_L^J = W_32^q, q < 16
   if constexpr (q == 0) {
     return d;
@@ -110,7 +102,7 @@ __device__ __forceinline__ float2 twc(float2 d) {
 }
 
 template <int R, int SPAN, int START, int J>
-__device__ __forceinline__ void dif_bfly(float2* v) {
+__host__ __device__ __forceinline__ void dif_bfly(float2* v) {
   if constexpr (J < SPAN) {
     float2 a = v[START + J], b = v[START + J + SPAN];
     v[START + J] = cadd(a, b);
@@ -119,14 +111,14 @@ __device__ __forceinline__ void dif_bfly(float2* v) {
   }
 }
 template <int R, int SPAN, int START>
-__device__ __forceinline__ void dif_stage(float2* v) {
+__host__ __device__ __forceinline__ void dif_stage(float2* v) {
   if constexpr (START < R) {
     dif_bfly<R, SPAN, START, 0>(v);
     dif_stage<R, SPAN, START + 2 * SPAN>(v);
   }
 }
 template <int R, int SPAN>
-__device__ __forceinline__ void dif_all(float2* v) {
+__host__ __device__ __forceinline__ void dif_all(float2* v) {
   if constexpr (SPAN >= 1) {
     dif_stage<R, SPAN, 0>(v);
     dif_all<R, SPAN / 2>(v);
@@ -138,7 +130,7 @@ __host__ __device__ constexpr int bitrev(int i, int R) {
   return r;
 }
 template <int R, int I>
-__device__ __forceinline__ void unscramble(float2* v) {
+__host__ __device__ __forceinline__ void unscramble(float2* v) {
   if constexpr (I < R) {
     constexpr int J = bitrev(I, R);
     if constexpr (J > I) { float2 t = v[I]; v[I] = v[J]; v[J] = t; }
@@ -147,12 +139,94 @@ __device__ __forceinline__ void unscramble(float2* v) {
 }
 // In-register R-point forward DFT, natural order in and out (radix-2 DIF network).
 template <int R>
-__device__ __forceinline__ void dft(float2* v) {
+__host__ __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R > 1) {
     dif_all<R, R / 2>(v);
     unscramble<R, 0>(v);
   }
 }
+
+// ----------------------------------------------------------------------------- pass pieces
+#ifdef __CUDA_ARCH__
+#define SCD_LDG(p) __ldg(p)
+#else
+#define SCD_LDG(p) (*(p))
+#endif
+
+// Index of entry e of the concatenated pass-twiddle table of a size-M plan with radices
+// (r0, r1, r2): entry off(s) + r p + k holds W_M^{k r M/(p R)} (k < p, r < R).
+__host__ __device__ inline int64_t pass_twiddle_exponent(int e, int M, int r0, int r1, int r2) {
+  const int n1 = r0 * r1;
+  int p, R, loc;
+  if (e < n1) { p = r0; R = r1; loc = e; }
+  else        { p = r0 * r1; R = r2; loc = e - n1; }
+  const int r = loc / p, k = loc % p;
+  return (int64_t)k * r * (M / (p * R));
+}
+
+// Per-thread pieces of the batched transform; registers v[] persist between pieces and
+// the caller separates the pieces that touch shared memory with barriers.
+template <int M>
+struct FftPieces {
+  using PI = PlanInfo<M>;
+  static constexpr int E = PI::E, T = PI::T;
+
+  // pass 0: E inputs of thread t straight from the producer, then an R0-point DFT
+  template <class Src>
+  __host__ __device__ __forceinline__ static void pass0_load(int c, int t, Src& src, float2* v) {
+    constexpr int R = PI::r0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src(c, t + r * (M / R));
+    dft<R>(v);
+  }
+  // pass 0 outputs of thread t to shared memory (A_{r0}[t, j] at j + t r0)
+  __host__ __device__ __forceinline__ static void pass0_store(int t, float2* reg, const float2* v) {
+    constexpr int R = PI::r0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) reg[spad(t * R + j)] = v[j];
+  }
+  // pass S >= 1: load from shared memory with twiddles and run the DFTs
+  template <int S>
+  __host__ __device__ __forceinline__ static void pass_load(int t, const float2* reg, const float2* tw, float2* v) {
+    constexpr int R = PI::R(S), p = PI::p(S), B = E / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = t + b * T;
+      const int k = i & (p - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float2 x = reg[spad(i + r * (M / R))];
+        if (r > 0) x = cmul(x, SCD_LDG(tw + PI::off(S) + r * p + k));
+        v[b * R + r] = x;
+      }
+      dft<R>(v + b * R);
+    }
+  }
+  // pass S outputs to shared memory (not the last pass)
+  template <int S>
+  __host__ __device__ __forceinline__ static void pass_store(int t, float2* reg, const float2* v) {
+    constexpr int R = PI::R(S), p = PI::p(S), B = E / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = t + b * T;
+      const int k = i & (p - 1);
+#pragma unroll
+      for (int j = 0; j < R; ++j) reg[spad((i - k) * R + k + p * j)] = v[b * R + j];
+    }
+  }
+  // outputs of the last pass S to the consumer (bin f in natural order)
+  template <int S, class Dst>
+  __host__ __device__ __forceinline__ static void pass_out(int c, int t, Dst& dst, const float2* v) {
+    constexpr int R = PI::R(S), p = PI::p(S), B = E / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int i = t + b * T;
+      const int k = i & (p - 1);
+#pragma unroll
+      for (int j = 0; j < R; ++j) dst(c, (i - k) * R + k + p * j, v[b * R + j]);
+    }
+  }
+};
 
 // ----------------------------------------------------------------------------- batched FFT
 // C transforms of size M per CTA, T = M/E threads each (blockDim.x == C*T).
@@ -169,84 +243,30 @@ template <int M, int C, bool CFAST, bool SYNC_DST, class Src, class Dst>
 __device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2* __restrict__ tw,
                                           Src& src, Dst& dst) {
   using PI = PlanInfo<M>;
+  using F = FftPieces<M>;
   constexpr int E = PI::E, T = PI::T;
   const int tid = threadIdx.x;
   const int c = CFAST ? (tid % C) : (tid / T);
   const int t = CFAST ? (tid / C) : (tid % T);
   float2* reg = sm + c * PI::stride();
   float2 v[E];
-
-  // ---- pass 0 (p = 1): read from the producer, no twiddles
-  constexpr int R0 = PI::r0;
-  static_assert(E == R0, "first pass must use the largest radix");
-  {
-    const int i = t;
-#pragma unroll
-    for (int r = 0; r < R0; ++r) v[r] = src(c, i + r * (M / R0));
-    dft<R0>(v);
-  }
+  F::pass0_load(c, t, src, v);
   if constexpr (PI::n == 1) {
-#pragma unroll
-    for (int j = 0; j < R0; ++j) dst(c, j, v[j]);
+    F::template pass_out<0>(c, t, dst, v);
   } else {
-#pragma unroll
-    for (int j = 0; j < R0; ++j) reg[spad(t * R0 + j)] = v[j];
+    F::pass0_store(t, reg, v);
     __syncthreads();
-    // ---- pass 1
-    constexpr int R1 = PI::r1, p1 = PI::p(1), B1 = E / R1;
-#pragma unroll
-    for (int b = 0; b < B1; ++b) {
-      const int i = t + b * T;
-      const int k = i & (p1 - 1);
-#pragma unroll
-      for (int r = 0; r < R1; ++r) {
-        float2 x = reg[spad(i + r * (M / R1))];
-        if (r > 0) x = cmul(x, __ldg(tw + PI::off(1) + r * p1 + k));
-        v[b * R1 + r] = x;
-      }
-      dft<R1>(v + b * R1);
-    }
+    F::template pass_load<1>(t, reg, tw, v);
     if constexpr (PI::n == 2) {
       if constexpr (SYNC_DST) __syncthreads();
-#pragma unroll
-      for (int b = 0; b < B1; ++b) {
-        const int i = t + b * T;
-        const int k = i & (p1 - 1);
-#pragma unroll
-        for (int j = 0; j < R1; ++j) dst(c, (i - k) * R1 + k + p1 * j, v[b * R1 + j]);
-      }
+      F::template pass_out<1>(c, t, dst, v);
     } else {
-      __syncthreads();                     // every read of this pass precedes the writes
-#pragma unroll
-      for (int b = 0; b < B1; ++b) {
-        const int i = t + b * T;
-        const int k = i & (p1 - 1);
-#pragma unroll
-        for (int j = 0; j < R1; ++j) reg[spad((i - k) * R1 + k + p1 * j)] = v[b * R1 + j];
-      }
+      __syncthreads();                     // every read of pass 1 precedes its writes
+      F::template pass_store<1>(t, reg, v);
       __syncthreads();
-      // ---- pass 2
-      constexpr int R2 = PI::r2, p2 = PI::p(2), B2 = E / R2;
-#pragma unroll
-      for (int b = 0; b < B2; ++b) {
-        const int i = t + b * T;
-        const int k = i & (p2 - 1);
-#pragma unroll
-        for (int r = 0; r < R2; ++r) {
-          float2 x = reg[spad(i + r * (M / R2))];
-          if (r > 0) x = cmul(x, __ldg(tw + PI::off(2) + r * p2 + k));
-          v[b * R2 + r] = x;
-        }
-        dft<R2>(v + b * R2);
-      }
+      F::template pass_load<2>(t, reg, tw, v);
       if constexpr (SYNC_DST) __syncthreads();
-#pragma unroll
-      for (int b = 0; b < B2; ++b) {
-        const int i = t + b * T;
-        const int k = i & (p2 - 1);
-#pragma unroll
-        for (int j = 0; j < R2; ++j) dst(c, (i - k) * R2 + k + p2 * j, v[b * R2 + j]);
-      }
+      F::template pass_out<2>(c, t, dst, v);
     }
   }
 }

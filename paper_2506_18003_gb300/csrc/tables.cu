@@ -31,16 +31,9 @@ __global__ void k_roots(float2* out, int64_t M) {
 // Stockham pass twiddles: for pass s (s >= 1) with p = prod of earlier radices and radix R,
 // entry off_s + r p + k = W_{pR}^{k r} = W_M^{k r M/(pR)} (k < p, r < R, so the index is < M).
 __global__ void k_pass(float2* out, int M, int r0, int r1, int r2) {
-  const int n1 = r0 * r1, n2 = r2 ? r0 * r1 * r2 : 0;
-  const int total = n1 + n2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    int p, R, loc;
-    if (e < n1) { p = r0; R = r1; loc = e; }
-    else        { p = r0 * r1; R = r2; loc = e - n1; }
-    const int r = loc / p, k = loc % p;
-    const int64_t j = (int64_t)k * r * (M / (p * R));
-    out[e] = root_fp64(j, M);
-  }
+  const int total = r0 * r1 + (r2 ? r0 * r1 * r2 : 0);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x)
+    out[e] = root_fp64(pass_twiddle_exponent(e, M, r0, r1, r2), M);
 }
 
 // W_N^{c m1'} for c < C, m1' < M1 at [m1'][c] (c m1' < C M1 <= N: no reduction needed)
