@@ -69,9 +69,29 @@ def kernel_bytes():
 STAGES = ["fam_channelise", "fam_pair_fft", "fam_map", "ssca_cdp", "ssca_cols", "ssca_rows", "ssca_map"]
 
 
+def captured_traffic(stage):
+    """DRAM bytes per launch of `stage` from the committed ncu capture (profiles/traffic.json),
+    or None when there is none or the kernel's sources changed since it was taken."""
+    import hashlib
+    try:
+        entry = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(stage)
+    except (OSError, ValueError):
+        return None
+    if not entry:
+        return None
+    h = hashlib.sha256()
+    try:
+        for f in entry["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+    except OSError:
+        return None
+    return entry["bytes_per_launch"] if h.hexdigest() == entry["sha256"] else None
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+    """Samples nvidia-smi SM clocks and throttle reasons every 100 ms; only the samples
+    taken while the `with` block (the timed region) runs are kept."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -79,30 +99,41 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.kept = []
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return self
+        threading.Thread(target=self._reader, daemon=True).start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0:      # sampler is up before timing starts
+            time.sleep(0.01)
+        self.start = len(self.lines)
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                self.out, _ = self.proc.communicate()
+        if self.proc is None:
+            return
+        self.kept = self.lines[self.start:]
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
 
     def summary(self):
-        if not getattr(self, "out", ""):
-            return None
-        rows = [r for r in csv.reader(io.StringIO(self.out)) if len(r) >= 9]
+        rows = [r for r in csv.reader(io.StringIO("".join(self.kept))) if len(r) >= 9]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -323,13 +354,7 @@ def run_ours(args):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = kb[top] / (stage_ms[top] * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(top)
-        except ValueError:
-            traffic = None
+    traffic = captured_traffic(top)
 
     ms_step = ms / args.steps
     value = world * samples_per_step() / (ms_step * 1e-3) / 1e6
@@ -402,7 +427,7 @@ def e2e(args, lib, binding, torch, stream, xf_np, xs_np, world):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "split"], default="fp32")

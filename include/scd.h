@@ -118,7 +118,7 @@ SCD_API size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision
  *   ah = (k - l) Q + q + P L   (alpha = (ah - P L)/(P L))
  * No two cells share a grid point; grid points no cell reaches are written as 0.
  *   S    complex64[Np][Np][P] (scd_fam's output)
- *   map  float32[2 Np][2 P L], fully overwritten
+ *   map  float32[2 Np][2 P L], 16-byte aligned, fully overwritten
  * Needs P L divisible by Np and 2 L <= Np (else SCD_ERR_UNSUPPORTED). */
 SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts);
 
@@ -127,7 +127,7 @@ SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, 
  *   ah = k N/Np + q + N                          (alpha = (ah - N)/N)
  *   fh = floor((k N/Np - q + N) / (2 N / Np))     (f = fh/Np - 1/2, bin width 1/Np)
  *   S    complex64[Np][N] (scd_ssca's output)
- *   map  float32[Np][2 N], fully overwritten (unreached points are 0) */
+ *   map  float32[Np][2 N], 16-byte aligned, fully overwritten (unreached points are 0) */
 SCD_API scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts);
 
 /* ------------------------------------------------------------------------------ host buffers

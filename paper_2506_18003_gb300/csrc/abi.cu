@@ -131,7 +131,7 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
 }
 
 scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts) {
-  if (!S || !map || !aligned(S, 16) || !aligned(map, 4)) return SCD_ERR_ARG;
+  if (!S || !map || !aligned(S, 16) || !aligned(map, 16)) return SCD_ERR_ARG;
   if (L < 1) return SCD_ERR_ARG;
   if (!np_ok(Np) || P < 2 || P > 16384 || !scd::is_pow2(P)) return SCD_ERR_UNSUPPORTED;
   if (((int64_t)P * L) % Np != 0 || 2 * (int64_t)L > Np) return SCD_ERR_UNSUPPORTED;
@@ -147,7 +147,7 @@ scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* m
 }
 
 scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts) {
-  if (!S || !map || !aligned(S, 16) || !aligned(map, 4)) return SCD_ERR_ARG;
+  if (!S || !map || !aligned(S, 16) || !aligned(map, 16)) return SCD_ERR_ARG;
   if (!np_ok(Np) || N < 4096 || N > (1 << 20) || !scd::is_pow2(N)) return SCD_ERR_UNSUPPORTED;
   const scd_opts& o = opts_or_default(opts);
   if (o.map_power != 1 && o.map_power != 2) return SCD_ERR_ARG;
