@@ -145,6 +145,26 @@ SCD_API scd_status scd_ssca_host(const void* x_host, int64_t N, int32_t Np, cons
                                  void* out_host, const scd_opts* opts);
 SCD_API size_t scd_ssca_host_workspace_bytes(int64_t N, int32_t Np, int32_t precision);
 
+/* ------------------------------------------------------------------------------ no allocation
+ * scd_fam_noalloc: scd_fam for callers that cannot allocate device memory when they run an
+ * estimate (for example a real-time receive loop that forbids allocation after start-up,
+ * because an allocation can synchronise the device and stall the sample stream, or a
+ * plug-in that is handed device pointers for its inputs and outputs and owns no memory).
+ * The paper has no counterpart to this entry point.
+ * Instead of a caller workspace and the library's cached tables it uses one fixed
+ * __device__ scratch array inside the library (about 2.25 MB, held by every GPU that loads
+ * the library until the process exits), and calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Arguments, output and results are those of scd_fam (opts->workspace is
+ * ignored), with one more limit: Np * P <= 262144 (e.g. Np = 256 with P <= 1024);
+ * larger sizes return SCD_ERR_UNSUPPORTED and scd_last_error() names the limit.
+ * All calls share the scratch array, which keeps the last call's contents (each call
+ * rewrites everything it reads, so nothing has to start at zero); calls whose executions
+ * overlap on the same GPU race on it and must be serialised by the caller.  The first call
+ * on a device resolves the array's device address (a one-time set-up per device); make
+ * that first call before any stream capture on that device. */
+SCD_API scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P,
+                                   const float* window, void* out, const scd_opts* opts);
+
 /* ------------------------------------------------------------------------------ timing
  * Helpers for opts->stage_events: create / destroy n CUDA events (with timing) on the
  * current device, and read the time between two recorded events (blocks until `end`

@@ -45,6 +45,7 @@ SIGNATURES = {
     "scd_fam_host_workspace_bytes": (_sz, [_i64, _i32, _i32, _i32, _i32]),
     "scd_ssca_host": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p]),
     "scd_ssca_host_workspace_bytes": (_sz, [_i64, _i32, _i32]),
+    "scd_fam_noalloc": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _opts_p]),
     "scd_events_create": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_events_destroy": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_event_elapsed_ms": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float)]),

@@ -129,4 +129,61 @@ cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream
   return cudaGetLastError();
 }
 
+cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
+                                const float2* wnp, const float2* tw, cudaStream_t st) {
+  cudaError_t err;
+  count_launches(1);
+#define SCD_K1W(NPV)                                                                       \
+  {                                                                                        \
+    constexpr int T = PlanInfo<NPV>::T;                                                    \
+    constexpr int C = (256 / T) < 1 ? 1 : 256 / T;                                         \
+    const int sm = smem_bytes<NPV>(C);                                                     \
+    if ((err = set_smem(k_fam_channelise<NPV, C>, sm)) != cudaSuccess) return err;         \
+    k_fam_channelise<NPV, C><<<(P + C - 1) / C, C * T, sm, st>>>(x, L, P, window, wnp, tw, X); \
+  }
+  switch (Np) {
+    case 16: SCD_K1W(16); break;
+    case 32: SCD_K1W(32); break;
+    case 64: SCD_K1W(64); break;
+    case 128: SCD_K1W(128); break;
+    case 256: SCD_K1W(256); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef SCD_K1W
+  return cudaGetLastError();
+}
+
+cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const float2* tw, cudaStream_t st) {
+  cudaError_t err;
+  const int64_t npairs = (int64_t)Np * Np;
+  count_launches(1);
+#define SCD_K2W(PV)                                                                        \
+  {                                                                                        \
+    constexpr int T = PlanInfo<PV>::T;                                                     \
+    constexpr int C = (256 / T) < 1 ? 1 : 256 / T;                                         \
+    const int sm = smem_bytes<PV>(C);                                                      \
+    if ((err = set_smem(k_fam_pairs<PV, C>, sm)) != cudaSuccess) return err;               \
+    k_fam_pairs<PV, C><<<(unsigned)((npairs + C - 1) / C), C * T, sm, st>>>(X, Np, out, tw); \
+  }
+  switch (P) {
+    case 2: SCD_K2W(2); break;
+    case 4: SCD_K2W(4); break;
+    case 8: SCD_K2W(8); break;
+    case 16: SCD_K2W(16); break;
+    case 32: SCD_K2W(32); break;
+    case 64: SCD_K2W(64); break;
+    case 128: SCD_K2W(128); break;
+    case 256: SCD_K2W(256); break;
+    case 512: SCD_K2W(512); break;
+    case 1024: SCD_K2W(1024); break;
+    case 2048: SCD_K2W(2048); break;
+    case 4096: SCD_K2W(4096); break;
+    case 8192: SCD_K2W(8192); break;
+    case 16384: SCD_K2W(16384); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef SCD_K2W
+  return cudaGetLastError();
+}
+
 }  // namespace scd

@@ -18,6 +18,11 @@ const float2* table_pass(int M, cudaError_t* err);         // Stockham pass twid
 const float2* table_cols(int N, int M1, int C, cudaError_t* err);  // W_N^{c m1'}, [m1'][c], c < C
 const float* table_hamming(int Np, cudaError_t* err);      // default window, float32
 void release_tables();
+// The same FP64 builders, writing into memory the caller provides (no allocation, no
+// synchronisation; enqueued on st).
+cudaError_t build_roots_into(float2* out, int M, cudaStream_t st);
+cudaError_t build_pass_into(float2* out, int M, cudaStream_t st);   // PlanInfo<M>::tw_len() entries
+cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st);
 
 // ---------------------------------------------------------------- FAM (fam.cu)
 // X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL + n] W_Np^{(k n) mod Np}
@@ -25,6 +30,11 @@ cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* w
                            cudaStream_t st);
 // out[kh][lh][qh] = sum_p X[kh][p] conj(X[lh][p]) W_P^{(q p) mod P}
 cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st);
+// The same two kernels with caller-provided tables (W_Np roots, pass twiddles of size Np
+// and of size P) instead of the cached ones.
+cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
+                                const float2* wnp, const float2* tw_np, cudaStream_t st);
+cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const float2* tw_p, cudaStream_t st);
 
 // ---------------------------------------------------------------- SSCA (ssca.cu)
 constexpr int kSscaCols = 8;       // columns m2 per CTA in the column pass
@@ -42,6 +52,8 @@ cudaError_t ssca_map(const float2* S, int64_t N, int Np, int power, float* map, 
 
 // ---------------------------------------------------------------- launch accounting
 void count_launches(int n);
+// Sets the text scd_last_error() returns on this thread.
+void set_last_error(const char* msg);
 
 // ---------------------------------------------------------------- helpers
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }

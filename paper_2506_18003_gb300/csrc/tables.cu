@@ -129,6 +129,25 @@ const float* table_hamming(int Np, cudaError_t* err) {
   });
 }
 
+cudaError_t build_roots_into(float2* out, int M, cudaStream_t st) {
+  k_roots<<<grid_for(M), 256, 0, st>>>(out, M);
+  return cudaGetLastError();
+}
+
+cudaError_t build_pass_into(float2* out, int M, cudaStream_t st) {
+  PassRadices r = pass_radices(M);
+  if (r.r0 == 0) return cudaErrorInvalidValue;
+  if (!r.r1) return cudaSuccess;                               // single-pass plans use no table
+  const int len = r.r0 * r.r1 + (r.r2 ? r.r0 * r.r1 * r.r2 : 0);
+  k_pass<<<grid_for(len), 256, 0, st>>>(out, M, r.r0, r.r1, r.r2);
+  return cudaGetLastError();
+}
+
+cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st) {
+  k_hamming<<<(Np + 255) / 256, 256, 0, st>>>(out, Np);
+  return cudaGetLastError();
+}
+
 void release_tables() {
   std::lock_guard<std::mutex> lock(g_mu);
   int cur = 0;
