@@ -172,6 +172,10 @@ SCD_API scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t
 SCD_API scd_status scd_events_create(int32_t n, void** events);
 SCD_API scd_status scd_events_destroy(int32_t n, void** events);
 SCD_API scd_status scd_event_elapsed_ms(void* start, void* end, float* ms);
+/* Synchronises `stream` and reports whether a kernel of this library on the current
+ * device gave up a bounded device-side wait since the last call (SCD_ERR_TIMEOUT; the
+ * affected estimate is invalid); clears the record.  SCD_OK otherwise. */
+SCD_API scd_status scd_check_device(void* stream);
 /* Number of kernels this library has launched in this process (all devices). */
 SCD_API uint64_t scd_launch_count(void);
 

@@ -49,6 +49,7 @@ SIGNATURES = {
     "scd_events_create": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_events_destroy": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_event_elapsed_ms": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "scd_check_device": (_i32, [_vp]),
     "scd_launch_count": (ctypes.c_uint64, []),
     "scd_prepare": (_i32, [_i32, _i64, _i32, _i32]),
     "scd_release_cache": (None, []),
@@ -195,6 +196,11 @@ def scd_ssca_map(S, N: int, Np: int, map=None, power: int = 1, stream=None):
     o = make_opts(stream, "fp32", None, power)
     check(lib.scd_ssca_map(_ptr(S), N, Np, _ptr(map), ctypes.byref(o)), "scd_ssca_map")
     return map
+
+
+def scd_check_device(stream=None) -> None:
+    """Raises ScdError(SCD_ERR_TIMEOUT) if a bounded device-side wait expired."""
+    check(load().scd_check_device(_stream(stream)), "scd_check_device")
 
 
 def scd_prepare(estimator: str, N: int, Np: int, P: int = 2) -> None:

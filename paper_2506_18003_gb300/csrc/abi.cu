@@ -88,7 +88,7 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
   scd_status s = check_fam(x, N, Np, L, P, window, out);
   if (s != SCD_OK) return s;
   const scd_opts& o = opts_or_default(opts);
-  if (o.precision != SCD_FP32) return SCD_ERR_UNSUPPORTED;
+  if (o.precision != SCD_FP32 && o.precision != SCD_SPLIT_BF16) return SCD_ERR_UNSUPPORTED;
   const size_t need = scd_fam_workspace_bytes(N, Np, L, P, o.precision);
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
@@ -101,9 +101,9 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
   float2* X = (float2*)o.workspace;
   StageMarks m{o, 3};
   if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::fam_channelise((const float2*)x, Np, L, P, window, X, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::fam_channelise((const float2*)x, Np, L, P, window, X, st, o.precision)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::fam_pair_fft(X, Np, P, (float2*)out, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::fam_pair_fft(X, Np, P, (float2*)out, st, o.precision)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(2, st)) != cudaSuccess) return cuda_fail(e);
   return SCD_OK;
 }
@@ -112,7 +112,7 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   scd_status s = check_ssca(x, N, Np, window, out);
   if (s != SCD_OK) return s;
   const scd_opts& o = opts_or_default(opts);
-  if (o.precision != SCD_FP32) return SCD_ERR_UNSUPPORTED;
+  if (o.precision != SCD_FP32 && o.precision != SCD_SPLIT_BF16) return SCD_ERR_UNSUPPORTED;
   const size_t need = scd_ssca_workspace_bytes(N, Np, o.precision);
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
@@ -125,11 +125,11 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   float2* ws = (float2*)o.workspace;
   StageMarks m{o, 4};
   if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::ssca_cdp((const float2*)x, N, Np, window, ws, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::ssca_cdp((const float2*)x, N, Np, window, ws, st, o.precision)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::ssca_cols(ws, N, Np, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::ssca_cols(ws, N, Np, st, o.precision)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(2, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::ssca_rows(ws, N, Np, (float2*)out, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::ssca_rows(ws, N, Np, (float2*)out, st, o.precision)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(3, st)) != cudaSuccess) return cuda_fail(e);
   return SCD_OK;
 }
@@ -286,6 +286,19 @@ scd_status scd_event_elapsed_ms(void* start, void* end, float* ms) {
   cudaError_t e = cudaEventSynchronize((cudaEvent_t)end);
   if (e == cudaSuccess) e = cudaEventElapsedTime(ms, (cudaEvent_t)start, (cudaEvent_t)end);
   return e == cudaSuccess ? SCD_OK : cuda_fail(e);
+}
+
+scd_status scd_check_device(void* stream) {
+  cudaError_t e;
+  unsigned* w = scd::device_error_word(&e);
+  if (!w) return cuda_fail(e);
+  if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e);
+  unsigned h = 0;
+  if ((e = cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+  if (h == 0) return SCD_OK;
+  if ((e = cudaMemset(w, 0, sizeof h)) != cudaSuccess) return cuda_fail(e);
+  scd::set_last_error("a bounded device-side wait expired");
+  return SCD_ERR_TIMEOUT;
 }
 
 uint64_t scd_launch_count(void) { return scd::g_launches.load(std::memory_order_relaxed); }

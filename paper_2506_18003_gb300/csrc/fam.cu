@@ -1,4 +1,6 @@
-// FAM kernels (FP32 form): K1 channeliser and K2 conjugate-product + P-point FFT.
+// FAM kernels: K1 channeliser and K2 conjugate-product + P-point FFT, each in the FP32 form
+// (CUDA-core radix butterflies) and the split-precision form (radix DFTs as bf16 hi/lo
+// tensor-core GEMMs with FP32 accumulation, fft_tc.cuh).
 //
 // K1 implements Eq. II.B-complex_demodulate_final with the block framing of Algorithm 1
 // (`Framing`, `Demodulate`): window, Np-point FFT, down-conversion W_Np^{(k p L) mod Np}
@@ -10,17 +12,25 @@
 // product array ever exists in memory), then the P-point FFT, and the fftshifted bins go
 // straight to out[kh][lh][qh].  X (Np*P*8 bytes, 2 MiB at Np=256, P=1024) stays in L2, so
 // the kernel's DRAM traffic is essentially the 8 Np^2 P output bytes.
-#include "fft.cuh"
+#include "fft_tc.cuh"
 #include "internal.h"
 
 namespace scd {
 namespace {
 
-template <int NP, int C>
+template <int M>
+struct Shape {                       // C transforms of size M per CTA, 256 threads (T <= 256)
+  static constexpr int T = PlanInfo<M>::T;
+  static constexpr int C = T >= 256 ? 1 : 256 / T;
+  static constexpr int THREADS = C * T;
+};
+
+template <int NP, int C, bool TC>
 __global__ void __launch_bounds__(C * PlanInfo<NP>::T)
 k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __restrict__ a,
-                 const float2* __restrict__ wnp, const float2* __restrict__ tw, float2* __restrict__ X) {
-  extern __shared__ float2 sm[];
+                 const float2* __restrict__ wnp, const float2* __restrict__ tw, float2* __restrict__ X,
+                 const unsigned char* __restrict__ bmats, unsigned* err) {
+  extern __shared__ __align__(128) float2 sm[];
   const int p0 = blockIdx.x * C;
   auto src = [&](int c, int n) -> float2 {
     const int p = p0 + c;
@@ -34,13 +44,14 @@ k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __rest
     const int kh = (f + NP / 2) & (NP - 1);
     X[(int64_t)kh * P + p] = cmul(v, __ldg(wnp + ((f * pl) & (NP - 1))));
   };
-  fft_batch<NP, C, true, false>(sm, tw, src, dst);
+  fft_run<NP, C, true, false, C * PlanInfo<NP>::T, TC, 0>(sm, tw, bmats, err, src, dst);
 }
 
-template <int PP, int C>
+template <int PP, int C, bool TC>
 __global__ void __launch_bounds__(C * PlanInfo<PP>::T)
-k_fam_pairs(const float2* __restrict__ X, int Np, float2* __restrict__ out, const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+k_fam_pairs(const float2* __restrict__ X, int Np, float2* __restrict__ out, const float2* __restrict__ tw,
+            const unsigned char* __restrict__ bmats, unsigned* err) {
+  extern __shared__ __align__(128) float2 sm[];
   const int64_t pair0 = (int64_t)blockIdx.x * C;
   const int64_t npairs = (int64_t)Np * Np;
   auto src = [&](int c, int p) -> float2 {
@@ -54,10 +65,8 @@ k_fam_pairs(const float2* __restrict__ X, int Np, float2* __restrict__ out, cons
     if (pair >= npairs) return;
     out[pair * PP + ((f + PP / 2) & (PP - 1))] = v;
   };
-  fft_batch<PP, C, false, false>(sm, tw, src, dst);
+  fft_run<PP, C, false, false, C * PlanInfo<PP>::T, TC, 0>(sm, tw, bmats, err, src, dst);
 }
-
-template <int M> constexpr int smem_bytes(int C) { return PlanInfo<M>::n == 1 ? 0 : C * PlanInfo<M>::stride() * (int)sizeof(float2); }
 
 template <class K>
 cudaError_t set_smem(K kernel, int bytes) {
@@ -65,125 +74,115 @@ cudaError_t set_smem(K kernel, int bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+template <int NPV, bool TC>
+cudaError_t launch_k1(const float2* x, int L, int P, const float* window, const float2* wnp, const float2* tw,
+                      float2* X, const unsigned char* bm, unsigned* err, cudaStream_t st) {
+  using S = Shape<NPV>;
+  constexpr int sm = FftSmem<NPV, S::C, S::THREADS, TC>::total;
+  cudaError_t e = set_smem(k_fam_channelise<NPV, S::C, TC>, sm);
+  if (e != cudaSuccess) return e;
+  k_fam_channelise<NPV, S::C, TC><<<(P + S::C - 1) / S::C, S::THREADS, sm, st>>>(x, L, P, window, wnp, tw, X, bm, err);
+  return cudaGetLastError();
+}
+
+template <int PV, bool TC>
+cudaError_t launch_k2(const float2* X, int Np, float2* out, const float2* tw, const unsigned char* bm, unsigned* err,
+                      cudaStream_t st) {
+  using S = Shape<PV>;
+  constexpr int sm = FftSmem<PV, S::C, S::THREADS, TC>::total;
+  cudaError_t e = set_smem(k_fam_pairs<PV, S::C, TC>, sm);
+  if (e != cudaSuccess) return e;
+  const int64_t npairs = (int64_t)Np * Np;
+  k_fam_pairs<PV, S::C, TC><<<(unsigned)((npairs + S::C - 1) / S::C), S::THREADS, sm, st>>>(X, Np, out, tw, bm, err);
+  return cudaGetLastError();
+}
+
+template <bool TC>
+cudaError_t dispatch_k1(int Np, const float2* x, int L, int P, const float* window, const float2* wnp,
+                        const float2* tw, float2* X, const unsigned char* bm, unsigned* err, cudaStream_t st) {
+  switch (Np) {
+    case 16: return launch_k1<16, TC>(x, L, P, window, wnp, tw, X, bm, err, st);
+    case 32: return launch_k1<32, TC>(x, L, P, window, wnp, tw, X, bm, err, st);
+    case 64: return launch_k1<64, TC>(x, L, P, window, wnp, tw, X, bm, err, st);
+    case 128: return launch_k1<128, TC>(x, L, P, window, wnp, tw, X, bm, err, st);
+    case 256: return launch_k1<256, TC>(x, L, P, window, wnp, tw, X, bm, err, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool TC>
+cudaError_t dispatch_k2(int P, const float2* X, int Np, float2* out, const float2* tw, const unsigned char* bm,
+                        unsigned* err, cudaStream_t st) {
+  switch (P) {
+    case 2: return launch_k2<2, TC>(X, Np, out, tw, bm, err, st);
+    case 4: return launch_k2<4, TC>(X, Np, out, tw, bm, err, st);
+    case 8: return launch_k2<8, TC>(X, Np, out, tw, bm, err, st);
+    case 16: return launch_k2<16, TC>(X, Np, out, tw, bm, err, st);
+    case 32: return launch_k2<32, TC>(X, Np, out, tw, bm, err, st);
+    case 64: return launch_k2<64, TC>(X, Np, out, tw, bm, err, st);
+    case 128: return launch_k2<128, TC>(X, Np, out, tw, bm, err, st);
+    case 256: return launch_k2<256, TC>(X, Np, out, tw, bm, err, st);
+    case 512: return launch_k2<512, TC>(X, Np, out, tw, bm, err, st);
+    case 1024: return launch_k2<1024, TC>(X, Np, out, tw, bm, err, st);
+    case 2048: return launch_k2<2048, TC>(X, Np, out, tw, bm, err, st);
+    case 4096: return launch_k2<4096, TC>(X, Np, out, tw, bm, err, st);
+    case 8192: return launch_k2<8192, TC>(X, Np, out, tw, bm, err, st);
+    case 16384: return launch_k2<16384, TC>(X, Np, out, tw, bm, err, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Tables of the split form for a size-M transform.
+cudaError_t tc_tables(int M, const unsigned char** bm, unsigned** ew) {
+  cudaError_t err;
+  int bytes = 0;
+  if (!(*bm = table_tc_bmats(M, &bytes, &err))) return err;
+  if (!(*ew = device_error_word(&err))) return err;
+  return cudaSuccess;
+}
+
 }  // namespace
 
-cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* window, float2* X, cudaStream_t st) {
+cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* window, float2* X, cudaStream_t st,
+                           int precision) {
   cudaError_t err;
   const float2* wnp = table_roots(Np, &err);
   if (!wnp) return err;
   const float2* tw = table_pass(Np, &err);
   if (!tw) return err;
   count_launches(1);
-#define SCD_K1(NPV)                                                                        \
-  {                                                                                        \
-    constexpr int T = PlanInfo<NPV>::T;                                                    \
-    constexpr int C = (256 / T) < 1 ? 1 : 256 / T;                                         \
-    const int sm = smem_bytes<NPV>(C);                                                     \
-    if ((err = set_smem(k_fam_channelise<NPV, C>, sm)) != cudaSuccess) return err;         \
-    k_fam_channelise<NPV, C><<<(P + C - 1) / C, C * T, sm, st>>>((const float2*)x, L, P, window, wnp, tw, X); \
+  if (precision == SCD_SPLIT_BF16) {
+    const unsigned char* bm;
+    unsigned* ew;
+    if ((err = tc_tables(Np, &bm, &ew)) != cudaSuccess) return err;
+    return dispatch_k1<true>(Np, x, L, P, window, wnp, tw, X, bm, ew, st);
   }
-  switch (Np) {
-    case 16: SCD_K1(16); break;
-    case 32: SCD_K1(32); break;
-    case 64: SCD_K1(64); break;
-    case 128: SCD_K1(128); break;
-    case 256: SCD_K1(256); break;
-    default: return cudaErrorInvalidValue;
-  }
-#undef SCD_K1
-  return cudaGetLastError();
+  return dispatch_k1<false>(Np, x, L, P, window, wnp, tw, X, nullptr, nullptr, st);
 }
 
-cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st) {
+cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st, int precision) {
   cudaError_t err;
   const float2* tw = table_pass(P, &err);
   if (!tw) return err;
-  const int64_t npairs = (int64_t)Np * Np;
   count_launches(1);
-#define SCD_K2(PV)                                                                         \
-  {                                                                                        \
-    constexpr int T = PlanInfo<PV>::T;                                                     \
-    constexpr int C = (256 / T) < 1 ? 1 : 256 / T;                                         \
-    const int sm = smem_bytes<PV>(C);                                                      \
-    if ((err = set_smem(k_fam_pairs<PV, C>, sm)) != cudaSuccess) return err;               \
-    k_fam_pairs<PV, C><<<(unsigned)((npairs + C - 1) / C), C * T, sm, st>>>(X, Np, out, tw); \
+  if (precision == SCD_SPLIT_BF16) {
+    const unsigned char* bm;
+    unsigned* ew;
+    if ((err = tc_tables(P, &bm, &ew)) != cudaSuccess) return err;
+    return dispatch_k2<true>(P, X, Np, out, tw, bm, ew, st);
   }
-  switch (P) {
-    case 2: SCD_K2(2); break;
-    case 4: SCD_K2(4); break;
-    case 8: SCD_K2(8); break;
-    case 16: SCD_K2(16); break;
-    case 32: SCD_K2(32); break;
-    case 64: SCD_K2(64); break;
-    case 128: SCD_K2(128); break;
-    case 256: SCD_K2(256); break;
-    case 512: SCD_K2(512); break;
-    case 1024: SCD_K2(1024); break;
-    case 2048: SCD_K2(2048); break;
-    case 4096: SCD_K2(4096); break;
-    case 8192: SCD_K2(8192); break;
-    case 16384: SCD_K2(16384); break;
-    default: return cudaErrorInvalidValue;
-  }
-#undef SCD_K2
-  return cudaGetLastError();
+  return dispatch_k2<false>(P, X, Np, out, tw, nullptr, nullptr, st);
 }
 
 cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
                                 const float2* wnp, const float2* tw, cudaStream_t st) {
-  cudaError_t err;
   count_launches(1);
-#define SCD_K1W(NPV)                                                                       \
-  {                                                                                        \
-    constexpr int T = PlanInfo<NPV>::T;                                                    \
-    constexpr int C = (256 / T) < 1 ? 1 : 256 / T;                                         \
-    const int sm = smem_bytes<NPV>(C);                                                     \
-    if ((err = set_smem(k_fam_channelise<NPV, C>, sm)) != cudaSuccess) return err;         \
-    k_fam_channelise<NPV, C><<<(P + C - 1) / C, C * T, sm, st>>>(x, L, P, window, wnp, tw, X); \
-  }
-  switch (Np) {
-    case 16: SCD_K1W(16); break;
-    case 32: SCD_K1W(32); break;
-    case 64: SCD_K1W(64); break;
-    case 128: SCD_K1W(128); break;
-    case 256: SCD_K1W(256); break;
-    default: return cudaErrorInvalidValue;
-  }
-#undef SCD_K1W
-  return cudaGetLastError();
+  return dispatch_k1<false>(Np, x, L, P, window, wnp, tw, X, nullptr, nullptr, st);
 }
 
 cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const float2* tw, cudaStream_t st) {
-  cudaError_t err;
-  const int64_t npairs = (int64_t)Np * Np;
   count_launches(1);
-#define SCD_K2W(PV)                                                                        \
-  {                                                                                        \
-    constexpr int T = PlanInfo<PV>::T;                                                     \
-    constexpr int C = (256 / T) < 1 ? 1 : 256 / T;                                         \
-    const int sm = smem_bytes<PV>(C);                                                      \
-    if ((err = set_smem(k_fam_pairs<PV, C>, sm)) != cudaSuccess) return err;               \
-    k_fam_pairs<PV, C><<<(unsigned)((npairs + C - 1) / C), C * T, sm, st>>>(X, Np, out, tw); \
-  }
-  switch (P) {
-    case 2: SCD_K2W(2); break;
-    case 4: SCD_K2W(4); break;
-    case 8: SCD_K2W(8); break;
-    case 16: SCD_K2W(16); break;
-    case 32: SCD_K2W(32); break;
-    case 64: SCD_K2W(64); break;
-    case 128: SCD_K2W(128); break;
-    case 256: SCD_K2W(256); break;
-    case 512: SCD_K2W(512); break;
-    case 1024: SCD_K2W(1024); break;
-    case 2048: SCD_K2W(2048); break;
-    case 4096: SCD_K2W(4096); break;
-    case 8192: SCD_K2W(8192); break;
-    case 16384: SCD_K2W(16384); break;
-    default: return cudaErrorInvalidValue;
-  }
-#undef SCD_K2W
-  return cudaGetLastError();
+  return dispatch_k2<false>(P, X, Np, out, tw, nullptr, nullptr, st);
 }
 
 }  // namespace scd

@@ -17,6 +17,10 @@ const float2* table_roots(int M, cudaError_t* err);        // W_M^j, j in [0, M)
 const float2* table_pass(int M, cudaError_t* err);         // Stockham pass twiddles of a size-M FFT
 const float2* table_cols(int N, int M1, int C, cudaError_t* err);  // W_N^{c m1'}, [m1'][c], c < C
 const float* table_hamming(int Np, cudaError_t* err);      // default window, float32
+// bf16 hi/lo complex-as-real DFT matrices of the radices of a size-M plan (tensor-core form)
+const unsigned char* table_tc_bmats(int M, int* bytes, cudaError_t* err);
+// one word per device, set by kernels whose bounded device-side waits expired
+unsigned* device_error_word(cudaError_t* err);
 void release_tables();
 // The same FP64 builders, writing into memory the caller provides (no allocation, no
 // synchronisation; enqueued on st).
@@ -26,10 +30,11 @@ cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st);
 
 // ---------------------------------------------------------------- FAM (fam.cu)
 // X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL + n] W_Np^{(k n) mod Np}
+// precision: SCD_FP32 or SCD_SPLIT_BF16 (radix DFTs as bf16 hi/lo tensor-core GEMMs)
 cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* window, float2* X,
-                           cudaStream_t st);
+                           cudaStream_t st, int precision);
 // out[kh][lh][qh] = sum_p X[kh][p] conj(X[lh][p]) W_P^{(q p) mod P}
-cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st);
+cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st, int precision);
 // The same two kernels with caller-provided tables (W_Np roots, pass twiddles of size Np
 // and of size P) instead of the cached ones.
 cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
@@ -40,11 +45,12 @@ cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const
 constexpr int kSscaCols = 8;       // columns m2 per CTA in the column pass
 void ssca_split(int64_t N, int* M1, int* M2);
 // Stage 0: channeliser + CDP, X_g into ws[kh][n]
-cudaError_t ssca_cdp(const float2* x, int64_t N, int Np, const float* window, float2* ws, cudaStream_t st);
+cudaError_t ssca_cdp(const float2* x, int64_t N, int Np, const float* window, float2* ws, cudaStream_t st,
+                     int precision);
 // Stage 1: M1-point column FFTs times the rotate factor, in place on ws
-cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st);
+cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st, int precision);
 // Stage 2: M2-point row FFTs, fftshifted into out[kh][sh]
-cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st);
+cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st, int precision);
 
 // ---------------------------------------------------------------- maps (map.cu)
 cudaError_t fam_map(const float2* S, int Np, int L, int P, int power, float* map, cudaStream_t st);

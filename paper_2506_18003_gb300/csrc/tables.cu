@@ -11,7 +11,9 @@
 #include <tuple>
 #include <vector>
 
-#include "fft.cuh"
+#include <cuda_bf16.h>
+
+#include "fft_tc.cuh"
 #include "internal.h"
 
 namespace scd {
@@ -41,6 +43,29 @@ __global__ void k_cols(float2* out, int64_t N, int M1, int C) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M1 * C; e += gridDim.x * blockDim.x) {
     const int m1 = e / C, c = e % C;
     out[e] = root_fp64(((int64_t)c * m1) % N, N);
+  }
+}
+
+// Complex-as-real DFT matrix of radix R for the tensor-core form, as bf16 hi and lo in the
+// canonical K-major layout (N = K = Kp rows/columns, zero beyond 2R):
+//   B[2j][2r] = B[2j+1][2r+1] = Re W_R^{jr},  B[2j][2r+1] = -Im W_R^{jr},  B[2j+1][2r] = Im W_R^{jr}
+// so that [Yr Yi] = [Xr Xi] B^T computes Y_j = sum_r X_r W_R^{jr}.
+__global__ void k_dftmat(unsigned char* out, int R, int Kp) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Kp * Kp; e += gridDim.x * blockDim.x) {
+    const int n = e / Kp, k = e % Kp;
+    double v = 0.0;
+    if (n < 2 * R && k < 2 * R) {
+      const int j = n >> 1, r = k >> 1;
+      double s, c;
+      sincospi(2.0 * (double)((j * r) % R) / (double)R, &s, &c);
+      const double wr = c, wi = -s;
+      v = (n & 1) == 0 ? ((k & 1) == 0 ? wr : -wi) : ((k & 1) == 0 ? wi : wr);
+    }
+    const __nv_bfloat16 hi = __double2bfloat16(v);
+    const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+    const uint32_t off = umma::kmajor_offset(n, k, Kp);
+    *reinterpret_cast<__nv_bfloat16*>(out + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(out + Kp * Kp * 2 + off) = lo;
   }
 }
 
@@ -146,6 +171,36 @@ cudaError_t build_pass_into(float2* out, int M, cudaStream_t st) {
 cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st) {
   k_hamming<<<(Np + 255) / 256, 256, 0, st>>>(out, Np);
   return cudaGetLastError();
+}
+
+// B matrices of every distinct radix of the size-M plan, concatenated in slot order
+// (the order TcPlan<M, *>::boff() expects).
+const unsigned char* table_tc_bmats(int M, int* bytes, cudaError_t* err) {
+  PassRadices r = pass_radices(M);
+  if (r.r0 == 0) { *err = cudaErrorInvalidValue; return nullptr; }
+  int radix[3] = {r.r0, r.r1, r.r2};
+  int nslots = 1, slot_radix[3] = {r.r0, 0, 0};
+  for (int s = 1; s < 3; ++s) {
+    if (!radix[s]) break;
+    bool seen = false;
+    for (int q = 0; q < nslots; ++q) seen |= slot_radix[q] == radix[s];
+    if (!seen) slot_radix[nslots++] = radix[s];
+  }
+  int total = 0, off[3];
+  for (int q = 0; q < nslots; ++q) { off[q] = total; total += 2 * tc_bmat_bytes(slot_radix[q]); }
+  *bytes = total;
+  return (const unsigned char*)get_or_build(4, M, 0, 0, (size_t)total, err, [&](void* p, cudaStream_t st) {
+    for (int q = 0; q < nslots; ++q) {
+      const int Kp = tc_kp(slot_radix[q]);
+      k_dftmat<<<grid_for((int64_t)Kp * Kp), 256, 0, st>>>((unsigned char*)p + off[q], slot_radix[q], Kp);
+    }
+  });
+}
+
+unsigned* device_error_word(cudaError_t* err) {
+  return (unsigned*)get_or_build(5, 0, 0, 0, 16, err, [&](void* p, cudaStream_t st) {
+    cudaMemsetAsync(p, 0, 16, st);
+  });
 }
 
 void release_tables() {
