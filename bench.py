@@ -280,7 +280,9 @@ def run_ours(args):
     binding.scd_prepare("fam", FAM["N"], Np, P)
     binding.scd_prepare("ssca", N, Ns)
 
-    def opts(events=None, off=0, n=0):
+    EV_PER_STEP = 11          # FAM 3, FAM map 2, SSCA 4, SSCA map 2
+
+    def opts(prec, events=None, off=0, n=0):
         o = binding.make_opts(stream, prec, work)
         if events is not None:
             o.stage_events = ctypes.cast(ctypes.addressof(events) + off * ctypes.sizeof(ctypes.c_void_p),
@@ -288,61 +290,67 @@ def run_ours(args):
             o.n_stage_events = n
         return o
 
-    EV_PER_STEP = 11          # FAM 3, FAM map 2, SSCA 4, SSCA map 2
-
-    def step(events=None, base=0):
-        o = opts(events, base + 0, 3)
+    def step(prec, events=None, base=0):
+        o = opts(prec, events, base + 0, 3)
         binding.check(lib.scd_fam(xf.data_ptr(), FAM["N"], Np, L, P, None, Sf.data_ptr(), ctypes.byref(o)), "fam")
-        o = opts(events, base + 3, 2)
+        o = opts(prec, events, base + 3, 2)
         o.map_power = 1
         binding.check(lib.scd_fam_map(Sf.data_ptr(), Np, L, P, Mf.data_ptr(), ctypes.byref(o)), "fam_map")
-        o = opts(events, base + 5, 4)
+        o = opts(prec, events, base + 5, 4)
         binding.check(lib.scd_ssca(xs.data_ptr(), N, Ns, None, Ss.data_ptr(), ctypes.byref(o)), "ssca")
-        o = opts(events, base + 9, 2)
+        o = opts(prec, events, base + 9, 2)
         o.map_power = 1
         binding.check(lib.scd_ssca_map(Ss.data_ptr(), N, Ns, Ms.data_ptr(), ctypes.byref(o)), "ssca_map")
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    nev = EV_PER_STEP * args.steps
-    events = (ctypes.c_void_p * nev)()
-    binding.check(lib.scd_events_create(nev, events), "events")
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize()
-    launches0 = lib.scd_launch_count()
-    with ClockSampler(local) as clk:
-        t_start.record(stream)
-        for s in range(args.steps):
-            step(events, EV_PER_STEP * s)
-        t_end.record(stream)
+    def timed(prec):
+        """W warm-up steps, then K steps bracketed by barrier + synchronize, per-stage events."""
+        for _ in range(args.warmup):
+            step(prec)
         torch.cuda.synchronize()
-    launches = lib.scd_launch_count() - launches0
-    barrier(world)
-    ms_local = t_start.elapsed_time(t_end)
-    ms = max_over_ranks(torch, ms_local, world)
+        binding.check(lib.scd_check_device(ctypes.c_void_p(stream.cuda_stream)), "device check")
+        nev = EV_PER_STEP * args.steps
+        events = (ctypes.c_void_p * nev)()
+        binding.check(lib.scd_events_create(nev, events), "events")
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = lib.scd_launch_count()
+        with ClockSampler(local) as clk:
+            t_start.record(stream)
+            for s in range(args.steps):
+                step(prec, events, EV_PER_STEP * s)
+            t_end.record(stream)
+            torch.cuda.synchronize()
+        launches = lib.scd_launch_count() - launches0
+        barrier(world)
+        binding.check(lib.scd_check_device(ctypes.c_void_p(stream.cuda_stream)), "device check")
+        ms = max_over_ranks(torch, t_start.elapsed_time(t_end), world)
 
-    def el(a, b):
-        f = ctypes.c_float()
-        binding.check(lib.scd_event_elapsed_ms(events[a], events[b], ctypes.byref(f)), "elapsed")
-        return f.value
+        def el(a, b):
+            f = ctypes.c_float()
+            binding.check(lib.scd_event_elapsed_ms(events[a], events[b], ctypes.byref(f)), "elapsed")
+            return f.value
 
-    stage_ms = {k: 0.0 for k in STAGES}
-    for s in range(args.steps):
-        b = EV_PER_STEP * s
-        stage_ms["fam_channelise"] += el(b + 0, b + 1)
-        stage_ms["fam_pair_fft"] += el(b + 1, b + 2)
-        stage_ms["fam_map"] += el(b + 3, b + 4)
-        stage_ms["ssca_cdp"] += el(b + 5, b + 6)
-        stage_ms["ssca_cols"] += el(b + 6, b + 7)
-        stage_ms["ssca_rows"] += el(b + 7, b + 8)
-        stage_ms["ssca_map"] += el(b + 9, b + 10)
-    lib.scd_events_destroy(nev, events)
-    for k in stage_ms:
-        stage_ms[k] /= args.steps
+        stage_ms = {k: 0.0 for k in STAGES}
+        for s in range(args.steps):
+            b = EV_PER_STEP * s
+            stage_ms["fam_channelise"] += el(b + 0, b + 1)
+            stage_ms["fam_pair_fft"] += el(b + 1, b + 2)
+            stage_ms["fam_map"] += el(b + 3, b + 4)
+            stage_ms["ssca_cdp"] += el(b + 5, b + 6)
+            stage_ms["ssca_cols"] += el(b + 6, b + 7)
+            stage_ms["ssca_rows"] += el(b + 7, b + 8)
+            stage_ms["ssca_map"] += el(b + 9, b + 10)
+        lib.scd_events_destroy(nev, events)
+        for k in stage_ms:
+            stage_ms[k] /= args.steps
+        return ms / args.steps, stage_ms, int(launches), clk.summary()
+
+    other = "split" if prec == "fp32" else "fp32"
+    ms_step, stage_ms, launches, clocks = timed(prec)
+    ms_other, stage_other, _, _ = timed(other)
+
     kb = kernel_bytes()
     top = max(stage_ms, key=stage_ms.get)
     peaks = {}
@@ -354,22 +362,27 @@ def run_ours(args):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = kb[top] / (stage_ms[top] * 1e-3) / 1e9
-    traffic = captured_traffic(top)
+    traffic = captured_traffic(top) if prec == "fp32" else None
 
-    ms_step = ms / args.steps
     value = world * samples_per_step() / (ms_step * 1e-3) / 1e6
+    dtype = {"fp32": "f32", "split": "bf16x3-split/f32-accumulate"}
     line = {
         "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3-split/f32-accumulate",
+        "vs_baseline": None, "dtype": dtype[prec],
         "data": "synthetic (seeded modulated signals of the paper's shapes)", "config": workload_desc(),
         "scd_points_per_s": world * points_per_step() / (ms_step * 1e-3),
-        "gpu_launches": int(launches),
+        "gpu_launches": launches,
         "stage_ms": {k: round(v, 5) for k, v in stage_ms.items()},
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes": kb[top]},
-        "clocks": clk.summary(),
+        "clocks": clocks,
+        "parity_gate": {"fp32": "max|dS|/max|S| <= 1e-5 (tests)", "split": "<= 1e-3 (tests)"},
+        other: {"value": world * samples_per_step() / (ms_other * 1e-3) / 1e6, "unit": "Msamples/s",
+                "ms_per_step": ms_other, "dtype": dtype[other],
+                "stage_ms": {k: round(v, 5) for k, v in stage_other.items()},
+                "speedup_vs_" + prec: ms_step / ms_other},
     }
     # per-kernel roofline fractions (context for the dominant one)
     line["stage_hbm_frac"] = {k: round(kb[k] / (stage_ms[k] * 1e-3) / 1e9 / hbm, 4) for k in STAGES if stage_ms[k] > 0}

@@ -130,6 +130,39 @@ SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, 
  *   map  float32[Np][2 N], 16-byte aligned, fully overwritten (unreached points are 0) */
 SCD_API scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts);
 
+/* ------------------------------------------------------------------------------ batches
+ * Batched form: nsig signals of uneven lengths through ONE persistent kernel launch (a
+ * device work queue of per-signal stage tiles with bounded dependency waits), captured in a
+ * CUDA graph that later runs with the same buffers and stream replay.
+ *   estimator  0 = FAM (Np, L), 1 = SSCA (Np; L ignored)
+ *   lengths    HOST array of nsig signal lengths (samples)
+ *   Np         power of two in [16, 256]; precision: scd_precision
+ * Per-signal transform sizes: FAM P_i = largest power of two with (P_i - 1) L + Np <= len_i
+ * (at most 8192); SSCA N_i = largest power of two <= len_i (in [2^12, 2^20]); the samples
+ * beyond are not used.  A signal too short for the smallest size gives SCD_ERR_ARG.
+ * The plan owns its task list and counters (device memory allocated here, freed by
+ * scd_batch_plan_destroy); the caller owns the arenas. */
+typedef struct scd_batch_plan scd_batch_plan;
+SCD_API scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np,
+                                         int32_t L, int32_t precision, scd_batch_plan** out);
+/* Layout of the arenas (any output pointer may be NULL):
+ *   x_offsets[nsig+1]    signal i is x_arena[x_offsets[i] .. x_offsets[i+1]) (its full length)
+ *   out_offsets[nsig+1]  its estimate starts at out_arena + out_offsets[i] (complex64 elements):
+ *                        FAM [Np][Np][P_i], SSCA [Np][N_i], as scd_fam / scd_ssca lay them out
+ *   sizes[nsig]          P_i (FAM) or N_i (SSCA);  used_len[nsig]  samples consumed
+ *   workspace_bytes      device workspace scd_batch_run needs */
+SCD_API scd_status scd_batch_query(const scd_batch_plan* plan, int64_t* x_offsets, int64_t* out_offsets,
+                                   int64_t* sizes, int64_t* used_len, size_t* workspace_bytes);
+/* Enqueues the whole batch on `stream` (a cudaStream_t; with NULL the kernel is launched
+ * directly instead of through a graph).  x_arena complex64[x_offsets[nsig]], out_arena
+ * complex64[out_offsets[nsig]], window float32[Np] or NULL (Hamming), workspace as queried.
+ * Runs of one plan must not overlap in time (they share the plan's counters).  A dependency
+ * wait that gives up (bounded at 2 s) sets the device error word: scd_check_device() then
+ * returns SCD_ERR_TIMEOUT. */
+SCD_API scd_status scd_batch_run(scd_batch_plan* plan, const void* x_arena, const float* window, void* out_arena,
+                                 void* workspace, void* stream);
+SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
+
 /* ------------------------------------------------------------------------------ host buffers
  * scd_fam_host / scd_ssca_host: the same estimates for HOST input and output buffers
  * (pinned memory gives full copy bandwidth; pageable memory works).  The call copies x

@@ -46,6 +46,13 @@ SIGNATURES = {
     "scd_ssca_host": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p]),
     "scd_ssca_host_workspace_bytes": (_sz, [_i64, _i32, _i32]),
     "scd_fam_noalloc": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _opts_p]),
+    "scd_batch_plan_create": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_int64), _i32, _i32, _i32,
+                                     ctypes.POINTER(ctypes.c_void_p)]),
+    "scd_batch_query": (_i32, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_size_t)]),
+    "scd_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "scd_batch_plan_destroy": (None, [_vp]),
     "scd_events_create": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_events_destroy": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_event_elapsed_ms": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float)]),
@@ -206,3 +213,56 @@ def scd_check_device(stream=None) -> None:
 def scd_prepare(estimator: str, N: int, Np: int, P: int = 2) -> None:
     lib = load()
     check(lib.scd_prepare({"fam": 0, "ssca": 1}[estimator], N, Np, P), "scd_prepare")
+
+
+class BatchPlan:
+    """A batch of uneven-length signals for one estimator (scd_batch_plan_* of the C ABI).
+
+    estimator: "fam" or "ssca"; lengths: signal lengths; the arenas are torch tensors:
+    x_arena complex64[x_offsets[-1]], out_arena complex64[out_offsets[-1]]."""
+
+    def __init__(self, estimator: str, lengths, Np: int, L: int = 1, precision="fp32"):
+        lib = load()
+        self.lib = lib
+        self.estimator = estimator
+        self.nsig = len(lengths)
+        self.Np, self.L = Np, L
+        arr = (ctypes.c_int64 * self.nsig)(*[int(v) for v in lengths])
+        handle = ctypes.c_void_p()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        check(lib.scd_batch_plan_create({"fam": 0, "ssca": 1}[estimator], self.nsig, arr, Np, L, prec,
+                                        ctypes.byref(handle)), "scd_batch_plan_create")
+        self.handle = handle
+        n = self.nsig
+        xo, oo = (ctypes.c_int64 * (n + 1))(), (ctypes.c_int64 * (n + 1))()
+        sz, used = (ctypes.c_int64 * n)(), (ctypes.c_int64 * n)()
+        ws = ctypes.c_size_t()
+        check(lib.scd_batch_query(handle, xo, oo, sz, used, ctypes.byref(ws)), "scd_batch_query")
+        self.x_offsets, self.out_offsets = list(xo), list(oo)
+        self.sizes, self.used = list(sz), list(used)
+        self.workspace_bytes = ws.value
+
+    def run(self, x_arena, out_arena, workspace, window=None, stream=None):
+        torch = _torch()
+        _need(x_arena, torch.complex64, self.x_offsets[-1], "x_arena")
+        _need(out_arena, torch.complex64, self.out_offsets[-1], "out_arena")
+        check(self.lib.scd_batch_run(self.handle, _ptr(x_arena), _ptr(window), _ptr(out_arena),
+                                     _ptr(workspace), _stream(stream)), "scd_batch_run")
+
+    def output(self, out_arena, i):
+        """View of signal i's estimate in the output arena."""
+        a, b = self.out_offsets[i], self.out_offsets[i + 1]
+        if self.estimator == "fam":
+            return out_arena[a:b].view(self.Np, self.Np, self.sizes[i])
+        return out_arena[a:b].view(self.Np, self.sizes[i])
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            self.lib.scd_batch_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -178,7 +178,7 @@ scd_status scd_prepare(int32_t estimator, int64_t N, int32_t Np, int32_t P) {
     int M1, M2;
     scd::ssca_split(N, &M1, &M2);
     if (!scd::table_roots((int)N, &e) || !scd::table_pass(M1, &e) || !scd::table_pass(M2, &e) ||
-        !scd::table_cols((int)N, M1, scd::kSscaCols, &e))
+        !scd::table_cols((int)N, M1, scd::ssca_cols_per_tile(M1), &e))
       return cuda_fail(e);
     return SCD_OK;
   }

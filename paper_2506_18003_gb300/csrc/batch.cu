@@ -1,0 +1,506 @@
+// Batched form: hundreds of signals of uneven lengths through ONE persistent launch per
+// estimator, captured in a CUDA graph.
+//
+// A batch plan lists tasks (one stage of one signal: FAM channeliser / pair FFT, SSCA
+// channeliser+CDP / column pass / row pass), each a range of tiles (one tile = one CTA's
+// share, the same tile functions the standalone kernels run).  The persistent kernel's CTAs
+// pull tile indices from a device counter in increasing order; a tile whose task depends on
+// an earlier task (same signal, previous stage) first waits until every tile of that task
+// has been published.  Dependencies always point to lower tile indices, and a tile is only
+// pulled by a running CTA, so the schedule cannot deadlock; every wait is still bounded (2 s
+// of device time), after which the tile is skipped and the device error word is set
+// (scd_batch_run then returns SCD_ERR_TIMEOUT).
+//
+// Per-signal sizes (uneven lengths, Sec. II with power-of-two transforms):
+//   FAM:  P_i = largest power of two with (P_i - 1) L + Np <= len_i, at most 8192;
+//   SSCA: N_i = largest power of two <= len_i, in [2^12, 2^20];
+// samples beyond those are not used.
+#include <stdio.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+#include "tiles.cuh"
+
+namespace scd {
+namespace {
+
+enum Op : int32_t { OP_FAM_CHAN = 0, OP_FAM_PAIRS = 1, OP_SSCA_CDP = 2, OP_SSCA_COLS = 3, OP_SSCA_ROWS = 4 };
+
+struct Task {
+  int32_t op, size, dep, bbytes;          // op, transform size, prerequisite task (-1), B bytes
+  int64_t first, tiles;                   // tile range [first, first + tiles)
+  int64_t x_off, out_off, ws_off;         // element offsets into the arenas
+  int32_t N, P, M1, M2;                   // the signal's sizes
+  const float2* tw;                       // pass twiddles of this task's transform size
+  const float2* wN;                       // SSCA column pass: W_N^j
+  const float2* cols;                     // SSCA column pass: W_N^{c m1'} at [m1'][c]
+  const unsigned char* bmats;             // split form: B matrices of this size
+};
+
+struct BatchArgs {
+  const Task* tasks;
+  int32_t ntasks, Np, L;
+  int64_t total;                          // tiles in the whole plan
+  unsigned* counters;                     // [0]: next tile, [1 + t]: tiles of task t done
+  const float2* x;                        // x arena
+  float2* out;                            // output arena
+  float2* ws;                             // workspace arena
+  const float* window;
+  const float2* wnp;                      // W_Np roots
+  const float2* tw_np;                    // pass twiddles of size Np
+  const unsigned char* bmats_np;          // split form: B matrices of size Np
+  int32_t bbytes_np;
+  unsigned* err;
+};
+
+constexpr int kThreads = 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bound on any dependency wait
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Shared-memory layout of the batch kernel: region 0 (largest over every size the estimator
+// may meet), then (split form) the largest B-matrix set, the tensor-core slot and slack.
+template <bool FAM, bool TC>
+struct BatchSmem {
+  template <int M, int EXTRA = 0>
+  using FS = FftSmem<M, TileShape<M>::C, TileShape<M>::NT, TC, EXTRA>;
+  static constexpr int mx(int a, int b) { return a > b ? a : b; }
+  static constexpr int fam_r0() {
+    return mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
+              mx(mx(FS<256>::region0, FS<512>::region0),
+                 mx(mx(FS<1024>::region0, FS<2048>::region0), mx(FS<4096>::region0, FS<8192>::region0))));
+  }
+  static constexpr int fam_b() {
+    return mx(mx(mx(FS<16>::bbytes, FS<32>::bbytes), mx(FS<64>::bbytes, FS<128>::bbytes)),
+              mx(mx(FS<256>::bbytes, FS<512>::bbytes),
+                 mx(mx(FS<1024>::bbytes, FS<2048>::bbytes), mx(FS<4096>::bbytes, FS<8192>::bbytes))));
+  }
+  static constexpr int ssca_r0() {
+    return mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
+              mx(mx(FS<256>::region0, FS<512>::region0),
+                 mx(mx(FS<1024>::region0, FS<64, rows_stage_bytes<64>()>::region0),
+                    mx(mx(FS<128, rows_stage_bytes<128>()>::region0, FS<256, rows_stage_bytes<256>()>::region0),
+                       mx(FS<512, rows_stage_bytes<512>()>::region0, FS<1024, rows_stage_bytes<1024>()>::region0)))));
+  }
+  static constexpr int ssca_b() {
+    return mx(mx(mx(FS<16>::bbytes, FS<32>::bbytes), mx(FS<64>::bbytes, FS<128>::bbytes)),
+              mx(mx(FS<256>::bbytes, FS<512>::bbytes), FS<1024>::bbytes));
+  }
+  static constexpr int region0 = FAM ? fam_r0() : ssca_r0();
+  static constexpr int bbytes = TC ? (FAM ? fam_b() : ssca_b()) : 0;
+  static constexpr int total = TC ? region0 + bbytes + 16 + 4096 : region0;
+  // TMEM columns: 256 threads, at most 32 values per thread, 2 fp32 columns per value
+  static constexpr int tmem_cols = 128;
+};
+
+template <bool TC>
+__device__ __forceinline__ void load_b(TcCtx& ctx, unsigned char* bsm, const unsigned char* bm, int bytes,
+                                       const unsigned char*& loaded) {
+  if constexpr (TC) {
+    if (loaded != bm) {
+      tc_load_b(ctx, bsm, bm, bytes);
+      loaded = bm;
+    }
+  }
+}
+
+template <bool TC>
+__device__ void fam_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
+                         const unsigned char*& loaded) {
+  const float2* x = A.x + t.x_off;
+  float2* X = A.ws + t.ws_off;
+  if (t.op == OP_FAM_CHAN) {
+    load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
+    switch (A.Np) {
+#define SCD_CH(NPV) case NPV: fam_channelise_tile<NPV, TC>(sm, ctx, x, A.L, t.P, A.window, A.wnp, A.tw_np, X, (int)tile * TileShape<NPV>::C); break;
+      SCD_CH(16) SCD_CH(32) SCD_CH(64) SCD_CH(128) SCD_CH(256)
+#undef SCD_CH
+    }
+  } else {
+    load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
+    float2* out = A.out + t.out_off;
+    switch (t.P) {
+#define SCD_PR(PV) case PV: fam_pairs_tile<PV, TC>(sm, ctx, X, A.Np, out, t.tw, tile * TileShape<PV>::C); break;
+      SCD_PR(2) SCD_PR(4) SCD_PR(8) SCD_PR(16) SCD_PR(32) SCD_PR(64) SCD_PR(128) SCD_PR(256) SCD_PR(512)
+      SCD_PR(1024) SCD_PR(2048) SCD_PR(4096) SCD_PR(8192)
+#undef SCD_PR
+    }
+  }
+}
+
+template <bool TC>
+__device__ void ssca_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
+                          const unsigned char*& loaded) {
+  const float2* x = A.x + t.x_off;
+  float2* ws = A.ws + t.ws_off;
+  if (t.op == OP_SSCA_CDP) {
+    load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
+    switch (A.Np) {
+#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, t.N, A.window, A.wnp, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
+      SCD_CD(16) SCD_CD(32) SCD_CD(64) SCD_CD(128) SCD_CD(256)
+#undef SCD_CD
+    }
+  } else if (t.op == OP_SSCA_COLS) {
+    load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
+    switch (t.M1) {
+#define SCD_CO(MV)                                                                          \
+  case MV: {                                                                                \
+    constexpr int C = TileShape<MV>::C;                                                     \
+    const int per = t.M2 / C;                                                               \
+    float2* row = ws + (int64_t)(tile / per) * t.N;                                         \
+    ssca_cols_tile<MV, TC>(sm, ctx, row, row, t.N, t.M2, t.wN, t.cols, t.tw, (int)(tile % per) * C); \
+  } break;
+      SCD_CO(64) SCD_CO(128) SCD_CO(256) SCD_CO(512) SCD_CO(1024)
+#undef SCD_CO
+    }
+  } else {
+    load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
+    float2* out = A.out + t.out_off;
+    switch (t.M2) {
+#define SCD_RO(MV)                                                                          \
+  case MV: {                                                                                \
+    constexpr int C = TileShape<MV>::C;                                                     \
+    const int per = t.M1 / C;                                                               \
+    const int64_t kh = tile / per;                                                          \
+    ssca_rows_tile<MV, TC>(sm, ctx, ws + kh * t.N, out + kh * t.N, t.M1, t.tw, (int)(tile % per) * C); \
+  } break;
+      SCD_RO(64) SCD_RO(128) SCD_RO(256) SCD_RO(512) SCD_RO(1024)
+#undef SCD_RO
+    }
+  }
+}
+
+template <bool FAM, bool TC>
+__global__ void __launch_bounds__(kThreads) k_batch(BatchArgs A) {
+  extern __shared__ __align__(128) float2 sm[];
+  __shared__ int64_t s_tile;
+  __shared__ int s_task;
+  __shared__ int s_skip;
+  using BS = BatchSmem<FAM, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  unsigned char* bsm = base + BS::region0;
+  if constexpr (TC) ctx = tc_open<BS::tmem_cols>(base + BS::region0 + BS::bbytes, A.err);
+  const unsigned char* loaded = nullptr;
+  for (;;) {
+    __syncthreads();                                         // previous tile fully done with smem
+    if (threadIdx.x == 0) {
+      const int64_t tile = (int64_t)atomicAdd(A.counters, 1u);
+      s_tile = tile;
+      int task = -1, skip = 0;
+      if (tile < A.total) {
+        int lo = 0, hi = A.ntasks - 1;                        // last task with first <= tile
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (A.tasks[mid].first <= tile) lo = mid; else hi = mid - 1;
+        }
+        task = lo;
+        const int dep = A.tasks[task].dep;
+        if (dep >= 0) {
+          const unsigned need = (unsigned)A.tasks[dep].tiles;
+          const unsigned long long t0 = globaltimer();
+          while (ld_acquire(A.counters + 1 + dep) < need) {
+            if (globaltimer() - t0 > kWaitNs) {
+              atomicOr(A.err, 2u);
+              skip = 1;
+              break;
+            }
+            __nanosleep(256);
+          }
+        }
+      }
+      s_task = task;
+      s_skip = skip;
+    }
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= A.total) break;
+    const Task& t = A.tasks[s_task];
+    if (!s_skip) {
+      if constexpr (FAM) fam_tile<TC>(A, t, tile - t.first, sm, ctx, bsm, loaded);
+      else ssca_tile<TC>(A, t, tile - t.first, sm, ctx, bsm, loaded);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(A.counters + 1 + s_task, 1u);
+    }
+  }
+  if constexpr (TC) tc_end<BS::tmem_cols>(ctx);
+}
+
+int smem_of(bool fam, bool tc) {
+  if (fam) return tc ? BatchSmem<true, true>::total : BatchSmem<true, false>::total;
+  return tc ? BatchSmem<false, true>::total : BatchSmem<false, false>::total;
+}
+
+template <bool FAM, bool TC>
+cudaError_t prepare_kernel(int smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch<FAM, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<FAM, TC>, kThreads, smem);
+}
+
+cudaError_t launch_batch(bool fam, bool tc, int grid, int smem, const BatchArgs& A, cudaStream_t st) {
+  if (fam) {
+    if (tc) k_batch<true, true><<<grid, kThreads, smem, st>>>(A);
+    else k_batch<true, false><<<grid, kThreads, smem, st>>>(A);
+  } else {
+    if (tc) k_batch<false, true><<<grid, kThreads, smem, st>>>(A);
+    else k_batch<false, false><<<grid, kThreads, smem, st>>>(A);
+  }
+  return cudaGetLastError();
+}
+
+int tile_c(int M) {                       // transforms per tile for size M (256 threads)
+  switch (M) {
+    case 2: return TileShape<2>::C;       case 4: return TileShape<4>::C;
+    case 8: return TileShape<8>::C;       case 16: return TileShape<16>::C;
+    case 32: return TileShape<32>::C;     case 64: return TileShape<64>::C;
+    case 128: return TileShape<128>::C;   case 256: return TileShape<256>::C;
+    case 512: return TileShape<512>::C;   case 1024: return TileShape<1024>::C;
+    case 2048: return TileShape<2048>::C; case 4096: return TileShape<4096>::C;
+    case 8192: return TileShape<8192>::C;
+    default: return 0;
+  }
+}
+
+}  // namespace
+}  // namespace scd
+
+struct scd_batch_plan {
+  int estimator = 0, nsig = 0, Np = 0, L = 0, precision = 0, device = 0;
+  std::vector<int64_t> x_off, out_off, ws_off, sizes, used;
+  std::vector<scd::Task> tasks;
+  scd::Task* d_tasks = nullptr;
+  unsigned* d_counters = nullptr;
+  int64_t total = 0;
+  size_t ws_bytes = 0;
+  int grid = 0, smem = 0;
+  const float2* wnp = nullptr;
+  const float2* tw_np = nullptr;
+  const unsigned char* bm_np = nullptr;
+  int bbytes_np = 0;
+  const float* hamming = nullptr;
+  unsigned* err = nullptr;
+  // cached graph of the last (x, window, out, workspace, stream) combination
+  cudaGraphExec_t exec = nullptr;
+  const void* g_x = nullptr;
+  const void* g_w = nullptr;
+  const void* g_out = nullptr;
+  const void* g_ws = nullptr;
+  void* g_stream = nullptr;
+};
+
+namespace {
+
+void free_plan(scd_batch_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->d_tasks) cudaFree(p->d_tasks);
+  if (p->d_counters) cudaFree(p->d_counters);
+  delete p;
+}
+
+scd_status cuda_status(cudaError_t e) {
+  char msg[160];
+  snprintf(msg, sizeof msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  scd::set_last_error(msg);
+  return SCD_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np, int32_t L,
+                                 int32_t precision, scd_batch_plan** out) {
+  using namespace scd;
+  if (!out || !lengths || nsig < 1 || (estimator != 0 && estimator != 1)) return SCD_ERR_ARG;
+  *out = nullptr;
+  if (Np < 16 || Np > 256 || !is_pow2(Np)) return SCD_ERR_UNSUPPORTED;
+  if (estimator == 0 && L < 1) return SCD_ERR_ARG;
+  if (precision != SCD_FP32 && precision != SCD_SPLIT_BF16) return SCD_ERR_UNSUPPORTED;
+  const bool fam = estimator == 0, tc = precision == SCD_SPLIT_BF16;
+  scd_batch_plan* p = new scd_batch_plan();
+  p->estimator = estimator; p->nsig = nsig; p->Np = Np; p->L = L; p->precision = precision;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+  p->x_off.assign(nsig + 1, 0); p->out_off.assign(nsig + 1, 0); p->ws_off.assign(nsig + 1, 0);
+  p->sizes.assign(nsig, 0); p->used.assign(nsig, 0);
+  for (int i = 0; i < nsig; ++i) {
+    const int64_t len = lengths[i];
+    if (len < 1) { free_plan(p); return SCD_ERR_ARG; }
+    int64_t sz = 0, used = 0;
+    if (fam) {
+      for (int64_t P = 8192; P >= 2; P >>= 1)
+        if ((P - 1) * L + Np <= len) { sz = P; break; }
+      used = (sz - 1) * L + Np;
+    } else {
+      for (int64_t n = 1 << 20; n >= 4096; n >>= 1)
+        if (n <= len) { sz = n; break; }
+      used = sz;
+    }
+    if (!sz) { free_plan(p); return SCD_ERR_ARG; }               // signal too short
+    p->sizes[i] = sz;
+    p->used[i] = used;
+    p->x_off[i + 1] = p->x_off[i] + len;
+    const int64_t outn = fam ? (int64_t)Np * Np * sz : (int64_t)Np * sz;
+    p->out_off[i + 1] = p->out_off[i] + outn;
+    p->ws_off[i + 1] = p->ws_off[i] + (int64_t)Np * sz;
+  }
+  p->ws_bytes = sizeof(float2) * (size_t)p->ws_off[nsig];
+  // tables
+  if (!(p->wnp = table_roots(Np, &e)) || !(p->tw_np = table_pass(Np, &e)) || !(p->hamming = table_hamming(Np, &e)) ||
+      !(p->err = device_error_word(&e))) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  if (tc && !(p->bm_np = table_tc_bmats(Np, &p->bbytes_np, &e))) { free_plan(p); return cuda_status(e); }
+  // tasks: every first stage, then the later stages signal by signal
+  const int cnp = tile_c(Np);
+  std::vector<Task>& T = p->tasks;
+  int64_t first = 0;
+  auto add = [&](Task t) { t.first = first; first += t.tiles; T.push_back(t); return (int)T.size() - 1; };
+  std::vector<int> stage0(nsig);
+  for (int i = 0; i < nsig; ++i) {
+    Task t{};
+    t.op = fam ? OP_FAM_CHAN : OP_SSCA_CDP;
+    t.size = Np;
+    t.dep = -1;
+    t.x_off = p->x_off[i]; t.out_off = p->out_off[i]; t.ws_off = p->ws_off[i];
+    if (fam) { t.P = (int)p->sizes[i]; t.tiles = (t.P + cnp - 1) / cnp; }
+    else { t.N = (int)p->sizes[i]; t.tiles = t.N / cnp; }
+    stage0[i] = add(t);
+  }
+  for (int i = 0; i < nsig; ++i) {
+    const int64_t sz = p->sizes[i];
+    if (fam) {
+      Task t = T[stage0[i]];
+      t.op = OP_FAM_PAIRS; t.size = (int)sz; t.dep = stage0[i];
+      const int c = tile_c((int)sz);
+      t.tiles = ((int64_t)Np * Np + c - 1) / c;
+      if (!(t.tw = table_pass((int)sz, &e))) { free_plan(p); return cuda_status(e); }
+      if (tc && !(t.bmats = table_tc_bmats((int)sz, &t.bbytes, &e))) { free_plan(p); return cuda_status(e); }
+      add(t);
+    } else {
+      int M1, M2;
+      ssca_split(sz, &M1, &M2);
+      Task c1 = T[stage0[i]];
+      c1.op = OP_SSCA_COLS; c1.size = M1; c1.dep = stage0[i]; c1.M1 = M1; c1.M2 = M2;
+      c1.tiles = (int64_t)Np * (M2 / tile_c(M1));
+      if (!(c1.tw = table_pass(M1, &e)) || !(c1.wN = table_roots((int)sz, &e)) ||
+          !(c1.cols = table_cols((int)sz, M1, tile_c(M1), &e))) {
+        free_plan(p);
+        return cuda_status(e);
+      }
+      if (tc && !(c1.bmats = table_tc_bmats(M1, &c1.bbytes, &e))) { free_plan(p); return cuda_status(e); }
+      const int ci = add(c1);
+      Task r = c1;
+      r.op = OP_SSCA_ROWS; r.size = M2; r.dep = ci;
+      r.tiles = (int64_t)Np * (M1 / tile_c(M2));
+      r.wN = nullptr; r.cols = nullptr; r.bmats = nullptr; r.bbytes = 0;
+      if (!(r.tw = table_pass(M2, &e))) { free_plan(p); return cuda_status(e); }
+      if (tc && !(r.bmats = table_tc_bmats(M2, &r.bbytes, &e))) { free_plan(p); return cuda_status(e); }
+      add(r);
+    }
+  }
+  p->total = first;
+  if (p->total >= (int64_t)0xFFFFFFF0u) { free_plan(p); return SCD_ERR_UNSUPPORTED; }
+  if ((e = cudaMalloc(&p->d_tasks, sizeof(Task) * T.size())) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_tasks, T.data(), sizeof(Task) * T.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_counters, sizeof(unsigned) * (T.size() + 1))) != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  p->smem = smem_of(fam, tc);
+  int per_sm = 0;
+  e = fam ? (tc ? prepare_kernel<true, true>(p->smem, &per_sm) : prepare_kernel<true, false>(p->smem, &per_sm))
+          : (tc ? prepare_kernel<false, true>(p->smem, &per_sm) : prepare_kernel<false, false>(p->smem, &per_sm));
+  if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+  int sms = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  if (tc && per_sm > 4) per_sm = 4;                              // 4 x 128 TMEM columns per SM
+  p->grid = sms * (per_sm > 0 ? per_sm : 1);
+  *out = p;
+  return SCD_OK;
+}
+
+scd_status scd_batch_query(const scd_batch_plan* p, int64_t* x_offsets, int64_t* out_offsets, int64_t* sizes,
+                           int64_t* used_len, size_t* workspace_bytes) {
+  if (!p) return SCD_ERR_ARG;
+  for (int i = 0; i <= p->nsig; ++i) {
+    if (x_offsets) x_offsets[i] = p->x_off[i];
+    if (out_offsets) out_offsets[i] = p->out_off[i];
+    if (i < p->nsig) {
+      if (sizes) sizes[i] = p->sizes[i];
+      if (used_len) used_len[i] = p->used[i];
+    }
+  }
+  if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+  return SCD_OK;
+}
+
+scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* window, void* out_arena, void* workspace,
+                         void* stream) {
+  using namespace scd;
+  if (!p || !x_arena || !out_arena || !workspace) return SCD_ERR_ARG;
+  if (((uintptr_t)x_arena % 8) || ((uintptr_t)out_arena % 16) || ((uintptr_t)workspace % 16) ||
+      (window && ((uintptr_t)window % 4)))
+    return SCD_ERR_ARG;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev != p->device) return SCD_ERR_ARG;
+  const float* w = window ? window : p->hamming;
+  cudaStream_t st = (cudaStream_t)stream;
+  BatchArgs A;
+  A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = p->Np; A.L = p->L; A.total = p->total;
+  A.counters = p->d_counters; A.x = (const float2*)x_arena; A.out = (float2*)out_arena; A.ws = (float2*)workspace;
+  A.window = w; A.wnp = p->wnp; A.tw_np = p->tw_np; A.bmats_np = p->bm_np; A.bbytes_np = p->bbytes_np; A.err = p->err;
+  const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
+  const size_t cbytes = sizeof(unsigned) * (p->tasks.size() + 1);
+  count_launches(1);
+  if (!st) {                                                    // legacy stream: no capture, plain launch
+    if ((e = cudaMemsetAsync(p->d_counters, 0, cbytes, st)) != cudaSuccess) return cuda_status(e);
+    e = launch_batch(fam, tc, p->grid, p->smem, A, st);
+    return e == cudaSuccess ? SCD_OK : cuda_status(e);
+  }
+  if (!p->exec || p->g_x != x_arena || p->g_w != (const void*)w || p->g_out != out_arena || p->g_ws != workspace ||
+      p->g_stream != stream) {
+    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_status(e);
+    cudaError_t e1 = cudaMemsetAsync(p->d_counters, 0, cbytes, st);
+    cudaError_t e2 = launch_batch(fam, tc, p->grid, p->smem, A, st);
+    e = cudaStreamEndCapture(st, &g);
+    if (e1 != cudaSuccess) e = e1;
+    if (e2 != cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) { p->exec = nullptr; return cuda_status(e); }
+    p->g_x = x_arena; p->g_w = w; p->g_out = out_arena; p->g_ws = workspace; p->g_stream = stream;
+  }
+  e = cudaGraphLaunch(p->exec, st);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
+}
+
+void scd_batch_plan_destroy(scd_batch_plan* p) { free_plan(p); }
+
+}  // extern "C"

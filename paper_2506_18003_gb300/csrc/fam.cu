@@ -12,60 +12,39 @@
 // product array ever exists in memory), then the P-point FFT, and the fftshifted bins go
 // straight to out[kh][lh][qh].  X (Np*P*8 bytes, 2 MiB at Np=256, P=1024) stays in L2, so
 // the kernel's DRAM traffic is essentially the 8 Np^2 P output bytes.
-#include "fft_tc.cuh"
 #include "internal.h"
+#include "tiles.cuh"
 
 namespace scd {
 namespace {
 
-template <int M>
-struct Shape {                       // C transforms of size M per CTA, 256 threads (T <= 256)
-  static constexpr int T = PlanInfo<M>::T;
-  static constexpr int C = T >= 256 ? 1 : 256 / T;
-  static constexpr int THREADS = C * T;
-};
-
-template <int NP, int C, bool TC>
-__global__ void __launch_bounds__(C * PlanInfo<NP>::T)
+template <int NP, bool TC>
+__global__ void __launch_bounds__(TileShape<NP>::NT)
 k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __restrict__ a,
                  const float2* __restrict__ wnp, const float2* __restrict__ tw, float2* __restrict__ X,
                  const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
-  const int p0 = blockIdx.x * C;
-  auto src = [&](int c, int n) -> float2 {
-    const int p = p0 + c;
-    if (p >= P) return make_float2(0.f, 0.f);
-    return cscale(__ldg(x + (int64_t)p * L + n), __ldg(a + n));
-  };
-  auto dst = [&](int c, int f, float2 v) {
-    const int p = p0 + c;
-    if (p >= P) return;
-    const int pl = (int)(((int64_t)p * L) & (NP - 1));          // (p L) mod Np
-    const int kh = (f + NP / 2) & (NP - 1);
-    X[(int64_t)kh * P + p] = cmul(v, __ldg(wnp + ((f * pl) & (NP - 1))));
-  };
-  fft_run<NP, C, true, false, C * PlanInfo<NP>::T, TC, 0>(sm, tw, bmats, err, src, dst);
+  using S = TileShape<NP>;
+  using FS = FftSmem<NP, S::C, S::NT, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
+  fam_channelise_tile<NP, TC>(sm, ctx, x, L, P, a, wnp, tw, X, blockIdx.x * S::C);
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int PP, int C, bool TC>
-__global__ void __launch_bounds__(C * PlanInfo<PP>::T)
+template <int PP, bool TC>
+__global__ void __launch_bounds__(TileShape<PP>::NT)
 k_fam_pairs(const float2* __restrict__ X, int Np, float2* __restrict__ out, const float2* __restrict__ tw,
             const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
-  const int64_t pair0 = (int64_t)blockIdx.x * C;
-  const int64_t npairs = (int64_t)Np * Np;
-  auto src = [&](int c, int p) -> float2 {
-    const int64_t pair = pair0 + c;
-    if (pair >= npairs) return make_float2(0.f, 0.f);
-    const int kh = (int)(pair / Np), lh = (int)(pair % Np);
-    return cmulc(__ldg(X + (int64_t)kh * PP + p), __ldg(X + (int64_t)lh * PP + p));
-  };
-  auto dst = [&](int c, int f, float2 v) {
-    const int64_t pair = pair0 + c;
-    if (pair >= npairs) return;
-    out[pair * PP + ((f + PP / 2) & (PP - 1))] = v;
-  };
-  fft_run<PP, C, false, false, C * PlanInfo<PP>::T, TC, 0>(sm, tw, bmats, err, src, dst);
+  using S = TileShape<PP>;
+  using FS = FftSmem<PP, S::C, S::NT, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
+  fam_pairs_tile<PP, TC>(sm, ctx, X, Np, out, tw, (int64_t)blockIdx.x * S::C);
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
 template <class K>
@@ -77,23 +56,23 @@ cudaError_t set_smem(K kernel, int bytes) {
 template <int NPV, bool TC>
 cudaError_t launch_k1(const float2* x, int L, int P, const float* window, const float2* wnp, const float2* tw,
                       float2* X, const unsigned char* bm, unsigned* err, cudaStream_t st) {
-  using S = Shape<NPV>;
-  constexpr int sm = FftSmem<NPV, S::C, S::THREADS, TC>::total;
-  cudaError_t e = set_smem(k_fam_channelise<NPV, S::C, TC>, sm);
+  using S = TileShape<NPV>;
+  constexpr int sm = FftSmem<NPV, S::C, S::NT, TC>::total;
+  cudaError_t e = set_smem(k_fam_channelise<NPV, TC>, sm);
   if (e != cudaSuccess) return e;
-  k_fam_channelise<NPV, S::C, TC><<<(P + S::C - 1) / S::C, S::THREADS, sm, st>>>(x, L, P, window, wnp, tw, X, bm, err);
+  k_fam_channelise<NPV, TC><<<(P + S::C - 1) / S::C, S::NT, sm, st>>>(x, L, P, window, wnp, tw, X, bm, err);
   return cudaGetLastError();
 }
 
 template <int PV, bool TC>
 cudaError_t launch_k2(const float2* X, int Np, float2* out, const float2* tw, const unsigned char* bm, unsigned* err,
                       cudaStream_t st) {
-  using S = Shape<PV>;
-  constexpr int sm = FftSmem<PV, S::C, S::THREADS, TC>::total;
-  cudaError_t e = set_smem(k_fam_pairs<PV, S::C, TC>, sm);
+  using S = TileShape<PV>;
+  constexpr int sm = FftSmem<PV, S::C, S::NT, TC>::total;
+  cudaError_t e = set_smem(k_fam_pairs<PV, TC>, sm);
   if (e != cudaSuccess) return e;
   const int64_t npairs = (int64_t)Np * Np;
-  k_fam_pairs<PV, S::C, TC><<<(unsigned)((npairs + S::C - 1) / S::C), S::THREADS, sm, st>>>(X, Np, out, tw, bm, err);
+  k_fam_pairs<PV, TC><<<(unsigned)((npairs + S::C - 1) / S::C), S::NT, sm, st>>>(X, Np, out, tw, bm, err);
   return cudaGetLastError();
 }
 

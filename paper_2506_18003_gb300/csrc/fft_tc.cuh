@@ -68,11 +68,10 @@ struct TcCtx {
 
 constexpr uint32_t kMbarPollLimit = 1u << 24;
 
-// Prologue: mbarrier init, TMEM allocation (warp 0), B matrices into shared memory.
-// `slot` points at 16 bytes of shared memory (mbarrier + TMEM address word).
+// Kernel prologue: mbarrier init and TMEM allocation (warp 0).  `slot` points at 16 bytes
+// of shared memory (mbarrier + TMEM address word).
 template <int NCOLS>
-__device__ __forceinline__ TcCtx tc_begin(unsigned char* slot, unsigned char* bsm, const unsigned char* bglobal,
-                                          int bbytes, unsigned* err) {
+__device__ __forceinline__ TcCtx tc_open(unsigned char* slot, unsigned* err) {
   uint64_t* mbar = reinterpret_cast<uint64_t*>(slot);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(slot + 8);
   if (threadIdx.x == 0) umma::mbar_init(mbar, 1);
@@ -80,8 +79,6 @@ __device__ __forceinline__ TcCtx tc_begin(unsigned char* slot, unsigned char* bs
     umma::tmem_alloc(tslot, NCOLS);
     umma::tmem_relinquish();
   }
-  for (int i = threadIdx.x * 16; i < bbytes; i += blockDim.x * 16)
-    *reinterpret_cast<uint4*>(bsm + i) = *reinterpret_cast<const uint4*>(bglobal + i);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -90,8 +87,26 @@ __device__ __forceinline__ TcCtx tc_begin(unsigned char* slot, unsigned char* bs
   c.tmem = *tslot;
   c.phase = 0;
   c.err = err;
-  c.bsm = bsm;
+  c.bsm = nullptr;
   c.ok = true;
+  return c;
+}
+
+// Copies the B matrices of the transform size about to run into shared memory.
+__device__ __forceinline__ void tc_load_b(TcCtx& c, unsigned char* bsm, const unsigned char* bglobal, int bbytes) {
+  __syncthreads();                                             // no MMA of the previous tile reads bsm
+  for (int i = threadIdx.x * 16; i < bbytes; i += blockDim.x * 16)
+    *reinterpret_cast<uint4*>(bsm + i) = *reinterpret_cast<const uint4*>(bglobal + i);
+  umma::fence_proxy_async();
+  __syncthreads();
+  c.bsm = bsm;
+}
+
+template <int NCOLS>
+__device__ __forceinline__ TcCtx tc_begin(unsigned char* slot, unsigned char* bsm, const unsigned char* bglobal,
+                                          int bbytes, unsigned* err) {
+  TcCtx c = tc_open<NCOLS>(slot, err);
+  tc_load_b(c, bsm, bglobal, bbytes);
   return c;
 }
 

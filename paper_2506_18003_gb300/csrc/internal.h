@@ -42,8 +42,8 @@ cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const flo
 cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const float2* tw_p, cudaStream_t st);
 
 // ---------------------------------------------------------------- SSCA (ssca.cu)
-constexpr int kSscaCols = 8;       // columns m2 per CTA in the column pass
 void ssca_split(int64_t N, int* M1, int* M2);
+int ssca_cols_per_tile(int M1);    // columns m2 per CTA of the column pass (256 threads)
 // Stage 0: channeliser + CDP, X_g into ws[kh][n]
 cudaError_t ssca_cdp(const float2* x, int64_t N, int Np, const float* window, float2* ws, cudaStream_t st,
                      int precision);

@@ -13,76 +13,55 @@
 //     stored fftshifted at sh = (q_nat + N/2) mod N = m1' + M1 ((m2' + M2/2) mod M2).  A CTA
 //     owns C2 consecutive rows m1' and transposes through shared memory so the strided
 //     output is written as runs of C2 contiguous values.
-#include "fft_tc.cuh"
 #include "internal.h"
+#include "tiles.cuh"
 
 namespace scd {
 namespace {
 
-constexpr int kC2 = 8;   // rows per CTA in the row pass (FP32 form)
-
-// Transforms per CTA: the FP32 form uses C_FP32; the tensor-core form needs a multiple of
-// 128 threads.
-template <int M, int C_FP32, bool TC>
-struct Batch {
-  static constexpr int T = PlanInfo<M>::T;
-  static constexpr int C = (TC && C_FP32 * T < 128) ? 128 / T : C_FP32;
-  static constexpr int THREADS = C * T;
-};
-
-template <int NP, int C, bool TC>
-__global__ void __launch_bounds__(C * PlanInfo<NP>::T)
+template <int NP, bool TC>
+__global__ void __launch_bounds__(TileShape<NP>::NT)
 k_ssca_cdp(const float2* __restrict__ x, int N, const float* __restrict__ a, const float2* __restrict__ wnp,
            const float2* __restrict__ tw, float2* __restrict__ Xg, const unsigned char* __restrict__ bmats,
            unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
-  const int n0 = blockIdx.x * C;
-  auto src = [&](int c, int r) -> float2 {
-    const int m = n0 + c - NP / 2 + r;
-    if (m < 0 || m >= N) return make_float2(0.f, 0.f);
-    return cscale(__ldg(x + m), __ldg(a + r));
-  };
-  auto dst = [&](int c, int f, float2 v) {
-    const int n = n0 + c;
-    const int s = (n - NP / 2) & (NP - 1);                        // s mod Np (s may be < 0)
-    const int kh = (f + NP / 2) & (NP - 1);
-    const float2 y = cmul(v, __ldg(wnp + ((f * s) & (NP - 1))));
-    Xg[(int64_t)kh * N + n] = cmulc(y, __ldg(x + n));
-  };
-  fft_run<NP, C, true, false, C * PlanInfo<NP>::T, TC, 0>(sm, tw, bmats, err, src, dst);
+  using S = TileShape<NP>;
+  using FS = FftSmem<NP, S::C, S::NT, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
+  ssca_cdp_tile<NP, TC>(sm, ctx, x, N, a, wnp, tw, Xg, blockIdx.x * S::C);
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int M1, int C, bool TC>
-__global__ void __launch_bounds__(C * PlanInfo<M1>::T)
+template <int M1, bool TC>
+__global__ void __launch_bounds__(TileShape<M1>::NT)
 k_ssca_cols(float2* __restrict__ Y, int N, int M2, const float2* __restrict__ wN, const float2* __restrict__ cols,
             const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
-  const int m20 = blockIdx.x * C;
-  float2* __restrict__ row = Y + (int64_t)blockIdx.y * N + m20;
-  auto src = [&](int c, int m1) -> float2 { return row[(int64_t)m1 * M2 + c]; };
-  auto dst = [&](int c, int f, float2 v) {
-    const float2 w = cmul(__ldg(wN + ((m20 * f) & (N - 1))), __ldg(cols + f * C + c));  // W_N^{(m20+c) f}
-    row[(int64_t)f * M2 + c] = cmul(v, w);
-  };
-  fft_run<M1, C, true, false, C * PlanInfo<M1>::T, TC, 0>(sm, tw, bmats, err, src, dst);
+  using S = TileShape<M1>;
+  using FS = FftSmem<M1, S::C, S::NT, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
+  float2* row = Y + (int64_t)blockIdx.y * N;
+  ssca_cols_tile<M1, TC>(sm, ctx, row, row, N, M2, wN, cols, tw, blockIdx.x * S::C);
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int M2, int C, bool TC>
-__global__ void __launch_bounds__(C * PlanInfo<M2>::T)
+template <int M2, bool TC>
+__global__ void __launch_bounds__(TileShape<M2>::NT)
 k_ssca_rows(const float2* __restrict__ Y, int N, int M1, const float2* __restrict__ tw, float2* __restrict__ out,
             const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
-  const int r0 = blockIdx.x * C;
-  const float2* __restrict__ in = Y + (int64_t)blockIdx.y * N + (int64_t)r0 * M2;
-  auto src = [&](int c, int m2) -> float2 { return in[c * M2 + m2]; };
-  auto dst = [&](int c, int f, float2 v) { sm[f * (C + 1) + c] = v; };
-  fft_run<M2, C, false, true, C * PlanInfo<M2>::T, TC, M2 * (C + 1) * 8>(sm, tw, bmats, err, src, dst);
-  __syncthreads();
-  float2* __restrict__ o = out + (int64_t)blockIdx.y * N + r0;
-  for (int e = threadIdx.x; e < C * M2; e += blockDim.x) {
-    const int c = e % C, f = e / C;
-    o[c + (int64_t)M1 * ((f + M2 / 2) & (M2 - 1))] = sm[f * (C + 1) + c];
-  }
+  using S = TileShape<M2>;
+  using FS = FftSmem<M2, S::C, S::NT, TC, rows_stage_bytes<M2>()>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
+  ssca_rows_tile<M2, TC>(sm, ctx, Y + (int64_t)blockIdx.y * N, out + (int64_t)blockIdx.y * N, M1, tw,
+                         blockIdx.x * S::C);
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
 template <class K>
@@ -108,40 +87,39 @@ cudaError_t tc_args(bool tc, int M, TcArgs* a) {
 template <int NPV, bool TC>
 cudaError_t launch_cdp_t(const float2* x, int N, const float* a, const float2* wnp, const float2* tw, float2* Xg,
                          TcArgs t, cudaStream_t st) {
-  constexpr int T = PlanInfo<NPV>::T;
-  constexpr int C = (256 / T) < 16 ? 16 : 256 / T;
-  constexpr int sm = FftSmem<NPV, C, C * T, TC>::total;
-  cudaError_t e = set_smem(k_ssca_cdp<NPV, C, TC>, sm);
+  using S = TileShape<NPV>;
+  constexpr int sm = FftSmem<NPV, S::C, S::NT, TC>::total;
+  cudaError_t e = set_smem(k_ssca_cdp<NPV, TC>, sm);
   if (e != cudaSuccess) return e;
-  k_ssca_cdp<NPV, C, TC><<<N / C, C * T, sm, st>>>(x, N, a, wnp, tw, Xg, t.bm, t.err);
+  k_ssca_cdp<NPV, TC><<<N / S::C, S::NT, sm, st>>>(x, N, a, wnp, tw, Xg, t.bm, t.err);
   return cudaGetLastError();
 }
 
 template <int MV, bool TC>
 cudaError_t launch_cols_t(float2* Y, int N, int Np, int M1, int M2, TcArgs t, cudaStream_t st) {
-  using B = Batch<MV, kSscaCols, TC>;
+  using S = TileShape<MV>;
   cudaError_t err;
   const float2* wN = table_roots(N, &err);
   if (!wN) return err;
-  const float2* cols = table_cols(N, M1, B::C, &err);
+  const float2* cols = table_cols(N, M1, S::C, &err);
   if (!cols) return err;
   const float2* tw = table_pass(M1, &err);
   if (!tw) return err;
-  constexpr int sm = FftSmem<MV, B::C, B::THREADS, TC>::total;
-  if ((err = set_smem(k_ssca_cols<MV, B::C, TC>, sm)) != cudaSuccess) return err;
-  k_ssca_cols<MV, B::C, TC><<<dim3(M2 / B::C, Np), B::THREADS, sm, st>>>(Y, N, M2, wN, cols, tw, t.bm, t.err);
+  constexpr int sm = FftSmem<MV, S::C, S::NT, TC>::total;
+  if ((err = set_smem(k_ssca_cols<MV, TC>, sm)) != cudaSuccess) return err;
+  k_ssca_cols<MV, TC><<<dim3(M2 / S::C, Np), S::NT, sm, st>>>(Y, N, M2, wN, cols, tw, t.bm, t.err);
   return cudaGetLastError();
 }
 
 template <int MV, bool TC>
 cudaError_t launch_rows_t(const float2* Y, int N, int Np, int M1, int M2, float2* out, TcArgs t, cudaStream_t st) {
-  using B = Batch<MV, kC2, TC>;
+  using S = TileShape<MV>;
   cudaError_t err;
   const float2* tw = table_pass(M2, &err);
   if (!tw) return err;
-  constexpr int sm = FftSmem<MV, B::C, B::THREADS, TC, MV * (B::C + 1) * 8>::total;
-  if ((err = set_smem(k_ssca_rows<MV, B::C, TC>, sm)) != cudaSuccess) return err;
-  k_ssca_rows<MV, B::C, TC><<<dim3(M1 / B::C, Np), B::THREADS, sm, st>>>(Y, N, M1, tw, out, t.bm, t.err);
+  constexpr int sm = FftSmem<MV, S::C, S::NT, TC, rows_stage_bytes<MV>()>::total;
+  if ((err = set_smem(k_ssca_rows<MV, TC>, sm)) != cudaSuccess) return err;
+  k_ssca_rows<MV, TC><<<dim3(M1 / S::C, Np), S::NT, sm, st>>>(Y, N, M1, tw, out, t.bm, t.err);
   return cudaGetLastError();
 }
 
@@ -201,6 +179,17 @@ cudaError_t launch_rows(const float2* Y, int N, int Np, int M1, int M2, float2* 
 }
 
 }  // namespace
+
+int ssca_cols_per_tile(int M1) {
+  switch (M1) {
+    case 64: return TileShape<64>::C;
+    case 128: return TileShape<128>::C;
+    case 256: return TileShape<256>::C;
+    case 512: return TileShape<512>::C;
+    case 1024: return TileShape<1024>::C;
+    default: return 0;
+  }
+}
 
 void ssca_split(int64_t N, int* M1, int* M2) {
   const int e = ilog2(N);

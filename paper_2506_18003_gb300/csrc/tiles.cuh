@@ -1,0 +1,134 @@
+// Tile functions: one CTA's share of each stage of the estimators, callable from the
+// standalone kernels (one tile per CTA) and from the persistent batch kernel (tiles pulled
+// from a device work queue).  Every tile function runs with THREADS = blockDim.x threads
+// and C = THREADS / T transforms, in the FP32 form or (TC) the split tensor-core form.
+#pragma once
+#include "fft_tc.cuh"
+
+namespace scd {
+
+// Transforms of size M handled by one CTA of THREADS threads.
+template <int M, int THREADS = 256>
+struct TileShape {
+  static constexpr int T = PlanInfo<M>::T;
+  static constexpr int C = T >= THREADS ? 1 : THREADS / T;
+  static constexpr int NT = C * T;                      // threads actually used
+};
+
+// Runs the C transforms of one tile in the requested form; for TC the caller has opened the
+// tensor-core context and loaded the B matrices of size M into ctx.bsm.
+template <int M, int C, bool CFAST, bool SYNC_DST, int THREADS, bool TC, class Src, class Dst>
+__device__ __forceinline__ void tile_fft(float2* sm, const float2* __restrict__ tw, TcCtx& ctx, Src& src, Dst& dst) {
+  if constexpr (TC) fft_batch_tc<M, C, CFAST, SYNC_DST, THREADS>(sm, tw, src, dst, ctx);
+  else fft_batch<M, C, CFAST, SYNC_DST>(sm, tw, src, dst);
+}
+
+// ---------------------------------------------------------------- FAM channeliser (K1)
+// frames p0 .. p0 + C - 1:  X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL+n] W_Np^{(k n) mod Np}
+template <int NP, bool TC>
+__device__ __forceinline__ void fam_channelise_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x, int L, int P,
+                                                    const float* __restrict__ a, const float2* __restrict__ wnp,
+                                                    const float2* __restrict__ tw, float2* __restrict__ X, int p0) {
+  using S = TileShape<NP>;
+  auto src = [&](int c, int n) -> float2 {
+    const int p = p0 + c;
+    if (p >= P) return make_float2(0.f, 0.f);
+    return cscale(__ldg(x + (int64_t)p * L + n), __ldg(a + n));
+  };
+  auto dst = [&](int c, int f, float2 v) {
+    const int p = p0 + c;
+    if (p >= P) return;
+    const int pl = (int)(((int64_t)p * L) & (NP - 1));          // (p L) mod Np
+    const int kh = (f + NP / 2) & (NP - 1);
+    X[(int64_t)kh * P + p] = cmul(v, __ldg(wnp + ((f * pl) & (NP - 1))));
+  };
+  tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+}
+
+// ---------------------------------------------------------------- FAM pair FFT (K2)
+// pairs pair0 .. pair0 + C - 1 (pair = kh Np + lh):
+//   out[kh][lh][qh] = sum_p X[kh][p] conj(X[lh][p]) W_P^{(q p) mod P}
+template <int PP, bool TC>
+__device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X, int Np,
+                                               float2* __restrict__ out, const float2* __restrict__ tw, int64_t pair0) {
+  using S = TileShape<PP>;
+  const int64_t npairs = (int64_t)Np * Np;
+  auto src = [&](int c, int p) -> float2 {
+    const int64_t pair = pair0 + c;
+    if (pair >= npairs) return make_float2(0.f, 0.f);
+    const int kh = (int)(pair / Np), lh = (int)(pair % Np);
+    return cmulc(__ldg(X + (int64_t)kh * PP + p), __ldg(X + (int64_t)lh * PP + p));
+  };
+  auto dst = [&](int c, int f, float2 v) {
+    const int64_t pair = pair0 + c;
+    if (pair >= npairs) return;
+    out[pair * PP + ((f + PP / 2) & (PP - 1))] = v;
+  };
+  tile_fft<PP, S::C, false, false, S::NT, TC>(sm, tw, ctx, src, dst);
+}
+
+// ---------------------------------------------------------------- SSCA channeliser + CDP (K3)
+// time points n0 .. n0 + C - 1:  X_g[kh][n] = W_Np^{(k s) mod Np} DFT_Np(a x[s ..])[k] conj(x[n])
+template <int NP, bool TC>
+__device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x, int N,
+                                              const float* __restrict__ a, const float2* __restrict__ wnp,
+                                              const float2* __restrict__ tw, float2* __restrict__ Xg, int n0) {
+  using S = TileShape<NP>;
+  auto src = [&](int c, int r) -> float2 {
+    const int m = n0 + c - NP / 2 + r;
+    if (m < 0 || m >= N) return make_float2(0.f, 0.f);
+    return cscale(__ldg(x + m), __ldg(a + r));
+  };
+  auto dst = [&](int c, int f, float2 v) {
+    const int n = n0 + c;
+    const int s = (n - NP / 2) & (NP - 1);                        // s mod Np (s may be < 0)
+    const int kh = (f + NP / 2) & (NP - 1);
+    const float2 y = cmul(v, __ldg(wnp + ((f * s) & (NP - 1))));
+    Xg[(int64_t)kh * N + n] = cmulc(y, __ldg(x + n));
+  };
+  tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+}
+
+// ---------------------------------------------------------------- SSCA column pass (K4a)
+// channel row `in` (N values, viewed [m1][m2], n = m1 M2 + m2), columns m20 .. m20 + C - 1:
+// M1-point DFT over m1, times the rotate factor W_N^{(m2 m1') mod N}, to `out` (may equal in)
+// at [m1'][m2].  wN = W_N^j table, cols = W_N^{c m1'} at [m1'][c].
+template <int M1, bool TC>
+__device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const float2* in, float2* out, int N, int M2,
+                                               const float2* __restrict__ wN, const float2* __restrict__ cols,
+                                               const float2* __restrict__ tw, int m20) {
+  using S = TileShape<M1>;
+  constexpr int C = S::C;
+  auto src = [&](int c, int m1) -> float2 { return in[(int64_t)m1 * M2 + m20 + c]; };
+  auto dst = [&](int c, int f, float2 v) {
+    const float2 w = cmul(__ldg(wN + ((m20 * f) & (N - 1))), __ldg(cols + f * C + c));  // W_N^{(m20+c) f}
+    out[(int64_t)f * M2 + m20 + c] = cmul(v, w);
+  };
+  tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+}
+
+// ---------------------------------------------------------------- SSCA row pass (K4b)
+// rows r0 .. r0 + C - 1 of one channel (`in` = [m1'][m2]): M2-point DFT over m2, output bin
+// q_nat = m1' + M1 m2' stored fftshifted at m1' + M1 ((m2' + M2/2) mod M2) of `out`; the
+// strided output is transposed through shared memory into runs of C contiguous values.
+template <int M2>
+__host__ __device__ constexpr int rows_stage_bytes() { return M2 * (TileShape<M2>::C + 1) * 8; }
+
+template <int M2, bool TC>
+__device__ __forceinline__ void ssca_rows_tile(float2* sm, TcCtx& ctx, const float2* in, float2* __restrict__ out,
+                                               int M1, const float2* __restrict__ tw, int r0) {
+  using S = TileShape<M2>;
+  constexpr int C = S::C;
+  const float2* rowp = in + (int64_t)r0 * M2;
+  auto src = [&](int c, int m2) -> float2 { return rowp[c * M2 + m2]; };
+  auto dst = [&](int c, int f, float2 v) { sm[f * (C + 1) + c] = v; };
+  tile_fft<M2, C, false, true, S::NT, TC>(sm, tw, ctx, src, dst);
+  __syncthreads();
+  float2* __restrict__ o = out + r0;
+  for (int e = threadIdx.x; e < C * M2; e += blockDim.x) {
+    const int c = e % C, f = e / C;
+    o[c + (int64_t)M1 * ((f + M2 / 2) & (M2 - 1))] = sm[f * (C + 1) + c];
+  }
+}
+
+}  // namespace scd

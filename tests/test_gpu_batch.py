@@ -1,0 +1,120 @@
+"""Batched form: uneven-length signals through one persistent (graph-captured) launch per
+estimator; every signal's estimate is compared with the FP64 oracle on the same input."""
+import numpy as np
+import pytest
+
+from oracle import scd_oracle as orc
+from paper_2506_18003_gb300 import binding, signals
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "split": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    binding.load()
+    return t
+
+
+def _arena(torch, sigs):
+    return torch.from_numpy(np.concatenate(sigs)).cuda()
+
+
+def _run(torch, plan, sigs, stream=None):
+    x = _arena(torch, sigs)
+    out = torch.empty(plan.out_offsets[-1], dtype=torch.complex64, device="cuda")
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    plan.run(x, out, ws, stream=stream)
+    binding.scd_check_device(stream)
+    return x, out, ws
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_fam_batch_every_signal(torch, precision):
+    Np, L = 64, 16
+    lengths = [4096, 5000, 1100, 8300, 4200, 2200, 17000, 3000]
+    sigs = [signals.batch_signal(i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("fam", lengths, Np, L, precision)
+    assert plan.sizes == [128, 256, 64, 512, 256, 128, 1024, 128]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _, out, _ = _run(torch, plan, sigs, s)
+    s.synchronize()
+    a = orc.hamming_window(Np)
+    for i, x in enumerate(sigs):
+        P = plan.sizes[i]
+        ref = orc.fam(x, a, Np, L, P)
+        got = plan.output(out, i).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL[precision], (i, err)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_ssca_batch_every_signal(torch, precision):
+    Np = 128
+    lengths = [4096, 6000, 16384, 9000, 40000, 4500]
+    sigs = [signals.batch_signal(100 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("ssca", lengths, Np, 1, precision)
+    assert plan.sizes == [4096, 4096, 16384, 8192, 32768, 4096]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _, out, _ = _run(torch, plan, sigs, s)
+    s.synchronize()
+    a = orc.hamming_window(Np)
+    for i, x in enumerate(sigs):
+        N = plan.sizes[i]
+        ref = orc.ssca(x[:N], a, Np)
+        got = plan.output(out, i).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL[precision], (i, err)
+    plan.close()
+
+
+def test_batch_graph_replay_is_bitwise_deterministic(torch):
+    Np, L = 64, 16
+    lengths = [5000, 9000, 4100, 20000]
+    sigs = [signals.batch_signal(200 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("fam", lengths, Np, L, "fp32")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        x, out, ws = _run(torch, plan, sigs, s)
+        first = out.clone()
+        for _ in range(3):                                    # graph replays
+            out.zero_()
+            plan.run(x, out, ws, stream=s)
+    s.synchronize()
+    binding.scd_check_device(s)
+    assert torch.equal(out, first)
+    plan.close()
+
+
+def test_batch_rejects_too_short_signal(torch):
+    with pytest.raises(binding.ScdError):
+        binding.BatchPlan("ssca", [5000, 1000], 128)
+
+
+def test_batch_512_signals_subset(torch):
+    """The 512-signal mixed workload (lengths log-uniform in [2^12, 2^18]), SSCA at Np=128:
+    all signals in one launch; the 4 shortest and 2 longest checked against the oracle."""
+    Np = 128
+    lengths = signals.batch_lengths()
+    sigs = [signals.batch_signal(i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("ssca", lengths, Np, 1, "fp32")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        _, out, _ = _run(torch, plan, sigs, s)
+    s.synchronize()
+    a = orc.hamming_window(Np)
+    order = np.argsort(lengths)
+    for i in list(order[:4]) + list(order[-2:]):
+        N = plan.sizes[i]
+        ch = np.array([0, 77, 127])
+        ref = orc.ssca(sigs[i][:N], a, Np, channels=ch)
+        got = plan.output(out, i)[torch.from_numpy(ch).cuda()].cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL["fp32"], (i, err)
+    plan.close()
