@@ -1,12 +1,19 @@
 #!/usr/bin/env python
-"""Benchmark of the SCD hot path (FAM + SSCA estimators and their (f, alpha) maps) on GB300.
+"""Benchmark of the SCD hot path (FAM + SSCA estimators) on GB300.
 
-One step = one pass of the whole path over one batch of synthetic input:
-  paper_scale (default): FAM at N=65,728 (Np=256, L=64, P=1024; 16-QAM) + its map, and
-                         SSCA at N=2^20 (Np=256; BPSK+QPSK mixture) + its map.
-The metric is input Msamples/s (samples consumed per second, whole job), with SCD points/s
-alongside.  Inputs are resident in HBM when the timed region starts; every step's working
-set (>2.5 GB of outputs) is larger than the 129 MB L2, so no flush is needed between steps.
+One step = one pass of the whole path over one batch of synthetic input.  Workloads:
+
+  batch (default)  512 signals, lengths log-uniform in [2^12, 2^18] (mixed BPSK / QPSK / 8-PSK /
+                   16-QAM / AM-DSB / noise), through FAM (Np=64, L=16) and SSCA (Np=128): one
+                   persistent, graph-captured launch per estimator.
+  paper_scale      one FAM estimate at N=65,728 (Np=256, L=64, P=1024) + its (f, alpha) map and
+                   one SSCA estimate at N=2^20 (Np=256) + its map.
+
+The metric is input Msamples/s: samples consumed per second by both estimators, whole job
+(SCD points/s alongside).  Both forms are timed: the FP32 form is the headline `value`, the
+split-precision form (bf16 hi/lo tensor-core GEMMs, FP32 accumulation) is reported beside it.
+Inputs are resident in HBM when the timed region starts; every step's working set is far
+larger than the 129 MB L2, so no flush is needed between steps.
 
 Prints ONE JSON line on rank 0.  --impl reference times the FP64 CPU oracle instead (the
 method's plain reference, on the host cores, on a bounded sample of the same workload).
@@ -14,11 +21,10 @@ method's plain reference, on the host cores, on a bounded sample of the same wor
 from __future__ import annotations
 
 import argparse
-import ctypes
 import csv
+import ctypes
 import io
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -30,43 +36,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "SCD input Msamples/s & points/s at stated error vs FP64; split-prec vs FP32 form"
-
-FAM = dict(N=65728, Np=256, L=64, P=1024)
-SSCA = dict(N=1 << 20, Np=256)
-
-
-def workload_desc():
-    return {"workload": "paper_scale: FAM N=65728 Np=256 L=64 P=1024 (16-QAM, RRC 0.25) + FAM map, "
-                        "SSCA N=2^20 Np=256 (BPSK+QPSK mixture, 0 dB) + SSCA map",
-            "fam": dict(FAM), "ssca": dict(SSCA), "window": "hamming",
-            "l2": "working set per step > L2 (no flush needed)"}
-
-
-def samples_per_step():
-    return FAM["N"] + SSCA["N"]
-
-
-def points_per_step():
-    return FAM["Np"] ** 2 * FAM["P"] + SSCA["Np"] * SSCA["N"]
-
-
-# Algorithmic (compulsory) bytes per launch of each kernel, complex64 = 8 B, float32 = 4 B.
-def kernel_bytes():
-    Np, L, P, Nf = FAM["Np"], FAM["L"], FAM["P"], FAM["N"]
-    N, Ns = SSCA["N"], SSCA["Np"]
-    Q = P * L // Np
-    return {
-        "fam_channelise": 8 * ((P - 1) * L + Np) + 8 * Np * P,
-        "fam_pair_fft": 8 * Np * Np * P,
-        "fam_map": 8 * Np * Np * 2 * Q + 4 * (2 * Np) * (2 * P * L),
-        "ssca_cdp": 8 * N + 8 * Ns * N,
-        "ssca_cols": 2 * 8 * Ns * N,
-        "ssca_rows": 2 * 8 * Ns * N,
-        "ssca_map": 8 * Ns * N + 4 * Ns * 2 * N,
-    }
-
-
-STAGES = ["fam_channelise", "fam_pair_fft", "fam_map", "ssca_cdp", "ssca_cols", "ssca_rows", "ssca_map"]
+DTYPE = {"fp32": "f32", "split": "bf16x3-split/f32-accumulate"}
 
 
 def captured_traffic(stage):
@@ -101,6 +71,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.kept = []
+        self.start = 0
 
     def _reader(self):
         for line in self.proc.stdout:
@@ -153,10 +124,8 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- distributed
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def max_over_ranks(torch, value, world):
@@ -174,82 +143,309 @@ def barrier(world):
         dist.barrier()
 
 
-# ----------------------------------------------------------------------------- CPU oracle
-_SIGNALS = {}
+# ----------------------------------------------------------------------------- workloads
+class BatchWorkload:
+    """512 mixed signals through the batched FAM and SSCA (one persistent launch each)."""
+    name = "batch"
+    FAM_NP, FAM_L, SSCA_NP = 64, 16, 128
+    stages = ["fam_batch", "ssca_batch"]
+    n_marks = 3
 
-
-def _bench_signals():
-    if not _SIGNALS:
+    def __init__(self, rank=0, count=512):
         from paper_2506_18003_gb300 import signals
-        _SIGNALS["fam"] = signals.fam_qam16_paper_scale()
-        _SIGNALS["ssca"] = signals.ssca_mixture_1m()
-    return _SIGNALS["fam"], _SIGNALS["ssca"]
+        self.lengths = [int(v) for v in signals.batch_lengths(count)]
+        # every rank processes its own independent signals (weak scaling)
+        self.sigs = [signals.batch_signal(i, n, seed=signals.seed_for(4, i + 1) + 7919 * rank)
+                     for i, n in enumerate(self.lengths)]
+        self.fam_P = [self._fam_P(n) for n in self.lengths]
+        self.ssca_N = [self._ssca_N(n) for n in self.lengths]
+
+    def _fam_P(self, n):
+        P = 8192
+        while (P - 1) * self.FAM_L + self.FAM_NP > n:
+            P //= 2
+        return P
+
+    @staticmethod
+    def _ssca_N(n):
+        N = 1 << 20
+        while N > n:
+            N //= 2
+        return N
+
+    def desc(self):
+        return {"workload": "batch: 512 signals, lengths log-uniform in [2^12, 2^18] (BPSK/QPSK/8PSK/16QAM/"
+                            "AM-DSB/AWGN, sps {2,4,8,16}, fc U(+-0.25), SNR U[-5,15] dB); FAM Np=64 L=16 "
+                            "(P_i = largest power of two that fits), SSCA Np=128 (N_i = largest power of two "
+                            "<= len_i); one persistent graph-captured launch per estimator",
+                "signals": len(self.lengths), "input_samples": int(sum(self.lengths)),
+                "fam": {"Np": self.FAM_NP, "L": self.FAM_L}, "ssca": {"Np": self.SSCA_NP},
+                "window": "hamming", "l2": "working set per step ~95 GB > L2 (no flush needed)"}
+
+    def fam_used(self):
+        return sum((P - 1) * self.FAM_L + self.FAM_NP for P in self.fam_P)
+
+    def samples_per_step(self):
+        return self.fam_used() + sum(self.ssca_N)
+
+    def points_per_step(self):
+        return sum(self.FAM_NP ** 2 * P for P in self.fam_P) + sum(self.SSCA_NP * N for N in self.ssca_N)
+
+    def kernel_bytes(self):
+        return {"fam_batch": 8 * self.fam_used() + 8 * sum(self.FAM_NP ** 2 * P for P in self.fam_P),
+                "ssca_batch": 8 * sum(self.ssca_N) + 8 * sum(self.SSCA_NP * N for N in self.ssca_N)}
+
+    def setup(self, torch, binding, dev, prec):
+        import numpy as np
+        self.torch, self.binding = torch, binding
+        self.x = torch.from_numpy(np.concatenate(self.sigs)).to(dev)
+        self.plans = {}
+        for p in ("fp32", "split"):
+            fam = binding.BatchPlan("fam", self.lengths, self.FAM_NP, self.FAM_L, p)
+            ssca = binding.BatchPlan("ssca", self.lengths, self.SSCA_NP, 1, p)
+            self.plans[p] = (fam, ssca)
+        fam, ssca = self.plans["fp32"]
+        self.out_f = torch.empty(fam.out_offsets[-1], dtype=torch.complex64, device=dev)
+        self.out_s = torch.empty(ssca.out_offsets[-1], dtype=torch.complex64, device=dev)
+        ws = max(fam.workspace_bytes, ssca.workspace_bytes)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=dev)
+
+    def step(self, prec, stream, marks=None):
+        fam, ssca = self.plans[prec]
+        if marks is not None:
+            marks[0].record(stream)
+        fam.run(self.x, self.out_f, self.ws, stream=stream)
+        if marks is not None:
+            marks[1].record(stream)
+        ssca.run(self.x, self.out_s, self.ws, stream=stream)
+        if marks is not None:
+            marks[2].record(stream)
+
+    def stage_times(self, marks):
+        return {"fam_batch": marks[0].elapsed_time(marks[1]), "ssca_batch": marks[1].elapsed_time(marks[2])}
+
+    def e2e(self, prec, stream, steps, world, torch):
+        """H2D of the input arena from pinned memory, both batched estimates, D2H of both
+        output arenas into pinned memory, every step (public Python binding)."""
+        xh = self.x.cpu().pin_memory()
+        of = torch.empty(self.out_f.shape, dtype=self.out_f.dtype).pin_memory()
+        os_ = torch.empty(self.out_s.shape, dtype=self.out_s.dtype).pin_memory()
+
+        def one():
+            self.x.copy_(xh, non_blocking=True)
+            self.step(prec, stream)
+            of.copy_(self.out_f, non_blocking=True)
+            os_.copy_(self.out_s, non_blocking=True)
+            stream.synchronize()
+
+        one()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        dt = max_over_ranks(torch, time.perf_counter() - t0, world)
+        return {"value": world * self.samples_per_step() * steps / dt / 1e6, "unit": "Msamples/s",
+                "h2d_bytes_per_step": xh.numel() * 8, "d2h_bytes_per_step": (of.numel() + os_.numel()) * 8,
+                "steps": steps, "api": "BatchPlan.run (scd_batch_run) with torch pinned-host copies in and out"}
+
+    def oracle_sample(self, nsig=3, reduced=False):
+        """FP64 oracle on `nsig` signals of the batch (FAM and SSCA each), extrapolated by
+        samples consumed to the whole step."""
+        import numpy as np
+        from oracle import scd_oracle as orc
+        order = np.argsort(self.lengths)
+        pick = [int(order[len(order) * (k + 1) // (nsig + 1)]) for k in range(nsig)]
+        af, as_ = orc.hamming_window(self.FAM_NP), orc.hamming_window(self.SSCA_NP)
+        used = 0
+        t0 = time.perf_counter()
+        for i in pick:
+            P, N = self.fam_P[i], self.ssca_N[i]
+            if reduced:                       # reference arm: a quarter of the pairs and channels
+                sel = np.arange(0, self.FAM_NP ** 2, 4)
+                orc.fam_pairs(self.sigs[i], af, self.FAM_NP, self.FAM_L, P, sel // self.FAM_NP, sel % self.FAM_NP)
+                used += ((P - 1) * self.FAM_L + self.FAM_NP) // 4
+                orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP, channels=np.arange(0, self.SSCA_NP, 4))
+                used += N // 4
+            else:
+                orc.fam(self.sigs[i], af, self.FAM_NP, self.FAM_L, P)
+                orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP)
+                used += (P - 1) * self.FAM_L + self.FAM_NP + N
+        t = time.perf_counter() - t0
+        what = "a quarter of the FAM pairs and SSCA channels" if reduced else "full FAM and SSCA estimates"
+        desc = (f"{nsig} signals of the batch (lengths {[self.lengths[i] for i in pick]}), {what}; time "
+                f"scaled by samples consumed ({used} of {self.samples_per_step()} per step)")
+        return t * self.samples_per_step() / used, desc
 
 
-def oracle_sample(fam_pairs: int, ssca_slice: int, ssca_rows: int, seed_offset: int = 0):
-    """Times the FP64 oracle on a bounded sample of the workload and extrapolates the
-    time of one full step (both estimators; the maps are not included).
-    Returns (seconds_per_full_step, description)."""
-    import numpy as np
+class PaperScaleWorkload:
+    """FAM N=65,728 Np=256 L=64 P=1024 + map, SSCA N=2^20 Np=256 + map."""
+    name = "paper_scale"
+    FAM = dict(N=65728, Np=256, L=64, P=1024)
+    SSCA = dict(N=1 << 20, Np=256)
+    stages = ["fam_channelise", "fam_pair_fft", "fam_map", "ssca_cdp", "ssca_cols", "ssca_rows", "ssca_map"]
+    n_marks = 11
 
-    from oracle import scd_oracle as orc
+    def __init__(self, rank=0):
+        from paper_2506_18003_gb300 import signals
+        self.wf = signals.fam_qam16_paper_scale(seed=signals.seed_for(2) + 100 * rank)
+        self.ws_ = signals.ssca_mixture_1m(seed=signals.seed_for(3) + 100 * rank)
 
-    wf, ws = _bench_signals()
-    Np, L, P = FAM["Np"], FAM["L"], FAM["P"]
-    a = orc.hamming_window(Np)
-    g = np.random.default_rng(17 + seed_offset)
-    kh = g.integers(0, Np, fam_pairs)
-    lh = g.integers(0, Np, fam_pairs)
-    t0 = time.perf_counter()
-    orc.fam_pairs(wf["x"], a, Np, L, P, kh, lh)
-    t_fam = (time.perf_counter() - t0) * (Np * Np / fam_pairs)
+    def desc(self):
+        return {"workload": "paper_scale: FAM N=65728 Np=256 L=64 P=1024 (16-QAM, RRC 0.25) + FAM map, "
+                            "SSCA N=2^20 Np=256 (BPSK+QPSK mixture, 0 dB) + SSCA map",
+                "fam": dict(self.FAM), "ssca": dict(self.SSCA), "window": "hamming",
+                "l2": "working set per step > L2 (no flush needed)"}
 
-    N, Ns = SSCA["N"], SSCA["Np"]
-    a2 = orc.hamming_window(Ns)
-    n0 = int(g.integers(0, N - ssca_slice))
-    t0 = time.perf_counter()
-    orc.ssca_cdp(ws["x"], a2, Ns, np.arange(n0, n0 + ssca_slice))
-    t_cdp = (time.perf_counter() - t0) * (N / ssca_slice)
-    row = (g.standard_normal((ssca_rows, N)) + 1j * g.standard_normal((ssca_rows, N)))
-    t0 = time.perf_counter()
-    for i in range(ssca_rows):
-        orc.ssca_strip(row[i])
-    t_strip = (time.perf_counter() - t0) * (Ns / ssca_rows)
-    desc = (f"FAM: {fam_pairs} of {Np * Np} channel pairs (oracle.fam_pairs, scaled x{Np * Np // fam_pairs}); "
-            f"SSCA: channeliser+CDP for {ssca_slice} of {N} samples (scaled x{N // ssca_slice}) + "
-            f"{ssca_rows} of {Ns} strip FFT rows (scaled x{Ns // ssca_rows}); maps not included")
-    return t_fam + t_cdp + t_strip, desc
+    def samples_per_step(self):
+        return self.FAM["N"] + self.SSCA["N"]
+
+    def points_per_step(self):
+        return self.FAM["Np"] ** 2 * self.FAM["P"] + self.SSCA["Np"] * self.SSCA["N"]
+
+    def kernel_bytes(self):
+        Np, L, P = self.FAM["Np"], self.FAM["L"], self.FAM["P"]
+        N, Ns = self.SSCA["N"], self.SSCA["Np"]
+        Q = P * L // Np
+        return {"fam_channelise": 8 * ((P - 1) * L + Np) + 8 * Np * P, "fam_pair_fft": 8 * Np * Np * P,
+                "fam_map": 8 * Np * Np * 2 * Q + 4 * (2 * Np) * (2 * P * L), "ssca_cdp": 8 * N + 8 * Ns * N,
+                "ssca_cols": 2 * 8 * Ns * N, "ssca_rows": 2 * 8 * Ns * N, "ssca_map": 8 * Ns * N + 4 * Ns * 2 * N}
+
+    def setup(self, torch, binding, dev, prec):
+        self.torch, self.binding = torch, binding
+        self.lib = binding.load()
+        F, S = self.FAM, self.SSCA
+        self.xf = torch.from_numpy(self.wf["x"]).to(dev)
+        self.xs = torch.from_numpy(self.ws_["x"]).to(dev)
+        self.Sf = torch.empty((F["Np"], F["Np"], F["P"]), dtype=torch.complex64, device=dev)
+        self.Ss = torch.empty((S["Np"], S["N"]), dtype=torch.complex64, device=dev)
+        self.Mf = torch.empty((2 * F["Np"], 2 * F["P"] * F["L"]), dtype=torch.float32, device=dev)
+        self.Ms = torch.empty((S["Np"], 2 * S["N"]), dtype=torch.float32, device=dev)
+        wsp = max(self.lib.scd_fam_workspace_bytes(F["N"], F["Np"], F["L"], F["P"], 0),
+                  self.lib.scd_ssca_workspace_bytes(S["N"], S["Np"], 0))
+        self.work = torch.empty(wsp, dtype=torch.uint8, device=dev)
+        binding.scd_prepare("fam", F["N"], F["Np"], F["P"])
+        binding.scd_prepare("ssca", S["N"], S["Np"])
+        self.events = None
+
+    def _opts(self, prec, stream, base, n):
+        o = self.binding.make_opts(stream, prec, self.work)
+        if self.events is not None:
+            o.stage_events = ctypes.cast(ctypes.addressof(self.events) + base * ctypes.sizeof(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_void_p))
+            o.n_stage_events = n
+        return o
+
+    def step(self, prec, stream, marks=None):
+        lib, chk, F, S = self.lib, self.binding.check, self.FAM, self.SSCA
+        self.events = marks
+        o = self._opts(prec, stream, 0, 3)
+        chk(lib.scd_fam(self.xf.data_ptr(), F["N"], F["Np"], F["L"], F["P"], None, self.Sf.data_ptr(),
+                        ctypes.byref(o)), "fam")
+        o = self._opts(prec, stream, 3, 2)
+        chk(lib.scd_fam_map(self.Sf.data_ptr(), F["Np"], F["L"], F["P"], self.Mf.data_ptr(), ctypes.byref(o)), "fam_map")
+        o = self._opts(prec, stream, 5, 4)
+        chk(lib.scd_ssca(self.xs.data_ptr(), S["N"], S["Np"], None, self.Ss.data_ptr(), ctypes.byref(o)), "ssca")
+        o = self._opts(prec, stream, 9, 2)
+        chk(lib.scd_ssca_map(self.Ss.data_ptr(), S["N"], S["Np"], self.Ms.data_ptr(), ctypes.byref(o)), "ssca_map")
+        self.events = None
+
+    def make_marks(self, n):
+        arr = (ctypes.c_void_p * n)()
+        self.binding.check(self.lib.scd_events_create(n, arr), "events")
+        return arr
+
+    def stage_times(self, ev):
+        def el(a, b):
+            f = ctypes.c_float()
+            self.binding.check(self.lib.scd_event_elapsed_ms(ev[a], ev[b], ctypes.byref(f)), "elapsed")
+            return f.value
+        return {"fam_channelise": el(0, 1), "fam_pair_fft": el(1, 2), "fam_map": el(3, 4), "ssca_cdp": el(5, 6),
+                "ssca_cols": el(6, 7), "ssca_rows": el(7, 8), "ssca_map": el(9, 10)}
+
+    def e2e(self, prec, stream, steps, world, torch):
+        lib, chk, F, S = self.lib, self.binding.check, self.FAM, self.SSCA
+        xf = torch.from_numpy(self.wf["x"]).pin_memory()
+        xs = torch.from_numpy(self.ws_["x"]).pin_memory()
+        of = torch.empty((F["Np"], F["Np"], F["P"]), dtype=torch.complex64).pin_memory()
+        os_ = torch.empty((S["Np"], S["N"]), dtype=torch.complex64).pin_memory()
+        need = max(lib.scd_fam_host_workspace_bytes(F["N"], F["Np"], F["L"], F["P"], 0),
+                   lib.scd_ssca_host_workspace_bytes(S["N"], S["Np"], 0))
+        work = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+        o = self.binding.make_opts(stream, prec, work)
+
+        def one():
+            chk(lib.scd_fam_host(xf.data_ptr(), F["N"], F["Np"], F["L"], F["P"], None, of.data_ptr(),
+                                 ctypes.byref(o)), "fam_host")
+            chk(lib.scd_ssca_host(xs.data_ptr(), S["N"], S["Np"], None, os_.data_ptr(), ctypes.byref(o)), "ssca_host")
+
+        one()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        dt = max_over_ranks(torch, time.perf_counter() - t0, world)
+        return {"value": world * self.samples_per_step() * steps / dt / 1e6, "unit": "Msamples/s",
+                "h2d_bytes_per_step": 8 * (F["N"] + S["N"]),
+                "d2h_bytes_per_step": 8 * (F["Np"] ** 2 * F["P"] + S["Np"] * S["N"]), "steps": steps,
+                "api": "scd_fam_host + scd_ssca_host (pinned host buffers, synchronous; maps not included)"}
+
+    def oracle_sample(self, reduced=False):
+        import numpy as np
+        from oracle import scd_oracle as orc
+        F, S = self.FAM, self.SSCA
+        pairs, nslice, rows = (256, 1 << 12, 1) if reduced else (2048, 1 << 15, 8)
+        g = np.random.default_rng(17)
+        a = orc.hamming_window(F["Np"])
+        t0 = time.perf_counter()
+        orc.fam_pairs(self.wf["x"], a, F["Np"], F["L"], F["P"], g.integers(0, F["Np"], pairs),
+                      g.integers(0, F["Np"], pairs))
+        t_fam = (time.perf_counter() - t0) * F["Np"] ** 2 / pairs
+        a2 = orc.hamming_window(S["Np"])
+        n0 = int(g.integers(0, S["N"] - nslice))
+        t0 = time.perf_counter()
+        orc.ssca_cdp(self.ws_["x"], a2, S["Np"], np.arange(n0, n0 + nslice))
+        t_cdp = (time.perf_counter() - t0) * S["N"] / nslice
+        row = g.standard_normal((rows, S["N"])) + 1j * g.standard_normal((rows, S["N"]))
+        t0 = time.perf_counter()
+        for i in range(rows):
+            orc.ssca_strip(row[i])
+        t_strip = (time.perf_counter() - t0) * S["Np"] / rows
+        desc = (f"FAM: {pairs} of {F['Np'] ** 2} pairs; SSCA: channeliser+CDP on {nslice} of {S['N']} samples + "
+                f"{rows} of {S['Np']} strip rows; each scaled linearly to the full workload; maps not included")
+        return t_fam + t_cdp + t_strip, desc
 
 
+WORKLOADS = {"batch": BatchWorkload, "paper_scale": PaperScaleWorkload}
+
+
+# ----------------------------------------------------------------------------- arms
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    steps = []
-    desc = ""
+    wl = WORKLOADS[args.workload]()
+    steps, desc = [], ""
     for i in range(args.warmup + args.steps):
-        t, desc = oracle_sample(fam_pairs=256, ssca_slice=1 << 12, ssca_rows=1, seed_offset=i)
+        t, desc = wl.oracle_sample(reduced=True)
         if i >= args.warmup:
             steps.append(t)
     t = statistics.mean(steps)
-    v = samples_per_step() / t / 1e6
+    v = wl.samples_per_step() / t / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Msamples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(),
+            "config": wl.desc(),
             "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step, " + desc + "; numpy FFT and elementwise kernels on one thread"},
+                             "sample": "per step: " + desc + "; numpy FFT and elementwise kernels on one thread"},
             "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-# ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
-    import numpy as np
     import torch
 
-    from paper_2506_18003_gb300 import binding, signals
+    from paper_2506_18003_gb300 import binding
 
     world, rank, local = dist_env()
     if not torch.cuda.is_available():
@@ -260,138 +456,89 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib = binding.load()
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    prec = args.precision
+    stream = torch.cuda.Stream(device=dev)
+    wl = WORKLOADS[args.workload](rank)
+    with torch.cuda.stream(stream):
+        wl.setup(torch, binding, dev, args.precision)
+    torch.cuda.synchronize()
 
-    # ---- inputs (seeded per rank: every rank processes its own independent signals)
-    wf = signals.fam_qam16_paper_scale(seed=signals.seed_for(2) + 100 * rank)
-    wsig = signals.ssca_mixture_1m(seed=signals.seed_for(3) + 100 * rank)
-    Np, L, P = FAM["Np"], FAM["L"], FAM["P"]
-    N, Ns = SSCA["N"], SSCA["Np"]
-    xf = torch.from_numpy(wf["x"]).to(dev)
-    xs = torch.from_numpy(wsig["x"]).to(dev)
-    Sf = torch.empty((Np, Np, P), dtype=torch.complex64, device=dev)
-    Ss = torch.empty((Ns, N), dtype=torch.complex64, device=dev)
-    Mf = torch.empty((2 * Np, 2 * P * L), dtype=torch.float32, device=dev)
-    Ms = torch.empty((Ns, 2 * N), dtype=torch.float32, device=dev)
-    wsp = max(lib.scd_fam_workspace_bytes(FAM["N"], Np, L, P, binding.PRECISIONS[prec]),
-              lib.scd_ssca_workspace_bytes(N, Ns, binding.PRECISIONS[prec]))
-    work = torch.empty(wsp, dtype=torch.uint8, device=dev)
-    binding.scd_prepare("fam", FAM["N"], Np, P)
-    binding.scd_prepare("ssca", N, Ns)
-
-    EV_PER_STEP = 11          # FAM 3, FAM map 2, SSCA 4, SSCA map 2
-
-    def opts(prec, events=None, off=0, n=0):
-        o = binding.make_opts(stream, prec, work)
-        if events is not None:
-            o.stage_events = ctypes.cast(ctypes.addressof(events) + off * ctypes.sizeof(ctypes.c_void_p),
-                                         ctypes.POINTER(ctypes.c_void_p))
-            o.n_stage_events = n
-        return o
-
-    def step(prec, events=None, base=0):
-        o = opts(prec, events, base + 0, 3)
-        binding.check(lib.scd_fam(xf.data_ptr(), FAM["N"], Np, L, P, None, Sf.data_ptr(), ctypes.byref(o)), "fam")
-        o = opts(prec, events, base + 3, 2)
-        o.map_power = 1
-        binding.check(lib.scd_fam_map(Sf.data_ptr(), Np, L, P, Mf.data_ptr(), ctypes.byref(o)), "fam_map")
-        o = opts(prec, events, base + 5, 4)
-        binding.check(lib.scd_ssca(xs.data_ptr(), N, Ns, None, Ss.data_ptr(), ctypes.byref(o)), "ssca")
-        o = opts(prec, events, base + 9, 2)
-        o.map_power = 1
-        binding.check(lib.scd_ssca_map(Ss.data_ptr(), N, Ns, Ms.data_ptr(), ctypes.byref(o)), "ssca_map")
+    def marks_for(n):
+        if hasattr(wl, "make_marks"):
+            return wl.make_marks(n)
+        return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
     def timed(prec):
-        """W warm-up steps, then K steps bracketed by barrier + synchronize, per-stage events."""
-        for _ in range(args.warmup):
-            step(prec)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                wl.step(prec, stream)
         torch.cuda.synchronize()
-        binding.check(lib.scd_check_device(ctypes.c_void_p(stream.cuda_stream)), "device check")
-        nev = EV_PER_STEP * args.steps
-        events = (ctypes.c_void_p * nev)()
-        binding.check(lib.scd_events_create(nev, events), "events")
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
+        binding.scd_check_device(stream)
+        marks = [marks_for(wl.n_marks) for _ in range(args.steps)]
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
         torch.cuda.synchronize()
         launches0 = lib.scd_launch_count()
-        with ClockSampler(local) as clk:
-            t_start.record(stream)
+        with ClockSampler(local) as clk, torch.cuda.stream(stream):
+            t0.record(stream)
             for s in range(args.steps):
-                step(prec, events, EV_PER_STEP * s)
-            t_end.record(stream)
+                wl.step(prec, stream, marks[s])
+            t1.record(stream)
             torch.cuda.synchronize()
         launches = lib.scd_launch_count() - launches0
         barrier(world)
-        binding.check(lib.scd_check_device(ctypes.c_void_p(stream.cuda_stream)), "device check")
-        ms = max_over_ranks(torch, t_start.elapsed_time(t_end), world)
+        binding.scd_check_device(stream)
+        ms = max_over_ranks(torch, t0.elapsed_time(t1), world)
+        stage = {k: 0.0 for k in wl.stages}
+        for m in marks:
+            for k, v in wl.stage_times(m).items():
+                stage[k] += v / args.steps
+        if hasattr(wl, "make_marks"):
+            for m in marks:
+                lib.scd_events_destroy(len(m), m)
+        return ms / args.steps, stage, int(launches), clk.summary()
 
-        def el(a, b):
-            f = ctypes.c_float()
-            binding.check(lib.scd_event_elapsed_ms(events[a], events[b], ctypes.byref(f)), "elapsed")
-            return f.value
-
-        stage_ms = {k: 0.0 for k in STAGES}
-        for s in range(args.steps):
-            b = EV_PER_STEP * s
-            stage_ms["fam_channelise"] += el(b + 0, b + 1)
-            stage_ms["fam_pair_fft"] += el(b + 1, b + 2)
-            stage_ms["fam_map"] += el(b + 3, b + 4)
-            stage_ms["ssca_cdp"] += el(b + 5, b + 6)
-            stage_ms["ssca_cols"] += el(b + 6, b + 7)
-            stage_ms["ssca_rows"] += el(b + 7, b + 8)
-            stage_ms["ssca_map"] += el(b + 9, b + 10)
-        lib.scd_events_destroy(nev, events)
-        for k in stage_ms:
-            stage_ms[k] /= args.steps
-        return ms / args.steps, stage_ms, int(launches), clk.summary()
-
+    prec = args.precision
     other = "split" if prec == "fp32" else "fp32"
     ms_step, stage_ms, launches, clocks = timed(prec)
     ms_other, stage_other, _, _ = timed(other)
 
-    kb = kernel_bytes()
+    kb = wl.kernel_bytes()
     top = max(stage_ms, key=stage_ms.get)
-    peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
-        pass
+        peaks = {}
     hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800 GB/s"
     hbm = hbm or 6800.0
     achieved = kb[top] / (stage_ms[top] * 1e-3) / 1e9
-    traffic = captured_traffic(top) if prec == "fp32" else None
-
-    value = world * samples_per_step() / (ms_step * 1e-3) / 1e6
-    dtype = {"fp32": "f32", "split": "bf16x3-split/f32-accumulate"}
+    value = world * wl.samples_per_step() / (ms_step * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": dtype[prec],
-        "data": "synthetic (seeded modulated signals of the paper's shapes)", "config": workload_desc(),
-        "scd_points_per_s": world * points_per_step() / (ms_step * 1e-3),
+        "vs_baseline": None, "dtype": DTYPE[prec],
+        "data": "synthetic (seeded modulated signals of the paper's shapes)", "config": wl.desc(),
+        "scd_points_per_s": world * wl.points_per_step() / (ms_step * 1e-3),
         "gpu_launches": launches,
         "stage_ms": {k: round(v, 5) for k, v in stage_ms.items()},
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes": kb[top]},
+                     "frac": achieved / hbm, "traffic": captured_traffic(top) if prec == "fp32" else None,
+                     "peak_source": peak_src, "algorithmic_bytes": kb[top]},
+        "stage_hbm_frac": {k: round(kb[k] / (v * 1e-3) / 1e9 / hbm, 4) for k, v in stage_ms.items() if v > 0},
         "clocks": clocks,
-        "parity_gate": {"fp32": "max|dS|/max|S| <= 1e-5 (tests)", "split": "<= 1e-3 (tests)"},
-        other: {"value": world * samples_per_step() / (ms_other * 1e-3) / 1e6, "unit": "Msamples/s",
-                "ms_per_step": ms_other, "dtype": dtype[other],
+        "parity_gate": {"fp32": "max|dS|/max|S| <= 1e-5 vs FP64 oracle (tests)",
+                        "split": "<= 1e-3 (tests; measured ~2e-6)"},
+        other: {"value": world * wl.samples_per_step() / (ms_other * 1e-3) / 1e6, "unit": "Msamples/s",
+                "ms_per_step": ms_other, "dtype": DTYPE[other],
                 "stage_ms": {k: round(v, 5) for k, v in stage_other.items()},
-                "speedup_vs_" + prec: ms_step / ms_other},
+                f"speedup_vs_{prec}": ms_step / ms_other},
     }
-    # per-kernel roofline fractions (context for the dominant one)
-    line["stage_hbm_frac"] = {k: round(kb[k] / (stage_ms[k] * 1e-3) / 1e9 / hbm, 4) for k in STAGES if stage_ms[k] > 0}
-
     if not args.no_e2e:
-        line["e2e"] = e2e(args, lib, binding, torch, stream, wf["x"], wsig["x"], world)
+        with torch.cuda.stream(stream):
+            line["e2e"] = wl.e2e(prec, stream, min(args.steps, args.e2e_steps), world, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, desc = oracle_sample(fam_pairs=2048, ssca_slice=1 << 15, ssca_rows=8)
-        line["cpu_baseline"] = {"value": samples_per_step() / t / 1e6, "unit": "Msamples/s", "cores": 1,
+        t, desc = wl.oracle_sample()
+        line["cpu_baseline"] = {"value": wl.samples_per_step() / t / 1e6, "unit": "Msamples/s", "cores": 1,
                                 "kind": "oracle", "sample": desc + "; numpy FFT and elementwise kernels on one thread"}
     if rank == 0:
         print(json.dumps(line))
@@ -401,54 +548,19 @@ def run_ours(args):
     return 0
 
 
-def e2e(args, lib, binding, torch, stream, xf_np, xs_np, world):
-    """Same metric through the host-buffer entry points: every step copies the inputs from
-    pinned host memory, runs both estimators and copies both estimates back."""
-    Np, L, P = FAM["Np"], FAM["L"], FAM["P"]
-    N, Ns = SSCA["N"], SSCA["Np"]
-    xf = torch.from_numpy(xf_np).pin_memory()
-    xs = torch.from_numpy(xs_np).pin_memory()
-    of = torch.empty((Np, Np, P), dtype=torch.complex64).pin_memory()
-    os_ = torch.empty((Ns, N), dtype=torch.complex64).pin_memory()
-    prec = binding.PRECISIONS[args.precision]
-    need = max(lib.scd_fam_host_workspace_bytes(FAM["N"], Np, L, P, prec),
-               lib.scd_ssca_host_workspace_bytes(N, Ns, prec))
-    work = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
-    o = binding.make_opts(stream, args.precision, work)
-
-    def step():
-        binding.check(lib.scd_fam_host(xf.data_ptr(), FAM["N"], Np, L, P, None, of.data_ptr(), ctypes.byref(o)), "fam_host")
-        binding.check(lib.scd_ssca_host(xs.data_ptr(), N, Ns, None, os_.data_ptr(), ctypes.byref(o)), "ssca_host")
-
-    for _ in range(max(1, args.warmup)):
-        step()
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    import torch as _t
-    dt = max_over_ranks(_t, dt, world)
-    del work
-    return {"value": world * samples_per_step() * args.steps / dt / 1e6, "unit": "Msamples/s",
-            "h2d_bytes_per_step": 8 * (FAM["N"] + N), "d2h_bytes_per_step": 8 * (Np * Np * P + Ns * N),
-            "api": "scd_fam_host + scd_ssca_host (pinned host buffers, synchronous)"}
-
-
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batch")
     ap.add_argument("--precision", choices=["fp32", "split"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

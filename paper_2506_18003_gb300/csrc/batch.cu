@@ -118,7 +118,7 @@ __device__ __forceinline__ void load_b(TcCtx& ctx, unsigned char* bsm, const uns
 }
 
 template <bool TC>
-__device__ void fam_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
+__device__ __forceinline__ void fam_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
                          const unsigned char*& loaded) {
   const float2* x = A.x + t.x_off;
   float2* X = A.ws + t.ws_off;
@@ -142,7 +142,7 @@ __device__ void fam_tile(const BatchArgs& A, const Task& t, int64_t tile, float2
 }
 
 template <bool TC>
-__device__ void ssca_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
+__device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
                           const unsigned char*& loaded) {
   const float2* x = A.x + t.x_off;
   float2* ws = A.ws + t.ws_off;
@@ -184,7 +184,7 @@ __device__ void ssca_tile(const BatchArgs& A, const Task& t, int64_t tile, float
 }
 
 template <bool FAM, bool TC>
-__global__ void __launch_bounds__(kThreads) k_batch(BatchArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs A) {
   extern __shared__ __align__(128) float2 sm[];
   __shared__ int64_t s_tile;
   __shared__ int s_task;
@@ -195,22 +195,24 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchArgs A) {
   unsigned char* bsm = base + BS::region0;
   if constexpr (TC) ctx = tc_open<BS::tmem_cols>(base + BS::region0 + BS::bbytes, A.err);
   const unsigned char* loaded = nullptr;
+  // Scheduling state, kept by thread 0: the next tile index is claimed one tile ahead so the
+  // atomic's latency overlaps the current tile; a CTA's tiles only increase, so the task is
+  // found by scanning forward; a satisfied dependency is remembered per task.
+  int64_t next = 0;
+  int cur = 0, dep_ok_task = -1;
+  if (threadIdx.x == 0) next = (int64_t)atomicAdd(A.counters, 1u);
   for (;;) {
     __syncthreads();                                         // previous tile fully done with smem
     if (threadIdx.x == 0) {
-      const int64_t tile = (int64_t)atomicAdd(A.counters, 1u);
+      const int64_t tile = next;
       s_tile = tile;
-      int task = -1, skip = 0;
+      int skip = 0;
       if (tile < A.total) {
-        int lo = 0, hi = A.ntasks - 1;                        // last task with first <= tile
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (A.tasks[mid].first <= tile) lo = mid; else hi = mid - 1;
-        }
-        task = lo;
-        const int dep = A.tasks[task].dep;
-        if (dep >= 0) {
-          const unsigned need = (unsigned)A.tasks[dep].tiles;
+        next = (int64_t)atomicAdd(A.counters, 1u);           // claim the following tile now
+        while (cur + 1 < A.ntasks && __ldg(&A.tasks[cur + 1].first) <= tile) ++cur;
+        const int dep = __ldg(&A.tasks[cur].dep);
+        if (dep >= 0 && dep_ok_task != cur) {
+          const unsigned need = (unsigned)__ldg(&A.tasks[dep].tiles);
           const unsigned long long t0 = globaltimer();
           while (ld_acquire(A.counters + 1 + dep) < need) {
             if (globaltimer() - t0 > kWaitNs) {
@@ -218,11 +220,12 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchArgs A) {
               skip = 1;
               break;
             }
-            __nanosleep(256);
+            __nanosleep(128);
           }
+          if (!skip) dep_ok_task = cur;
         }
       }
-      s_task = task;
+      s_task = cur;
       s_skip = skip;
     }
     __syncthreads();
@@ -370,13 +373,15 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     return cuda_status(e);
   }
   if (tc && !(p->bm_np = table_tc_bmats(Np, &p->bbytes_np, &e))) { free_plan(p); return cuda_status(e); }
-  // tasks: every first stage, then the later stages signal by signal
+  // Task order.  FAM: every channeliser task (tiny), then every pair task.  SSCA: software-
+  // pipelined by signal (cdp_s, cols_{s-1}, rows_{s-2}, ...), so a signal's intermediate is
+  // consumed soon after it is produced (small signals stay in L2) and every dependency has
+  // another task queued between it and its consumer.
   const int cnp = tile_c(Np);
   std::vector<Task>& T = p->tasks;
   int64_t first = 0;
   auto add = [&](Task t) { t.first = first; first += t.tiles; T.push_back(t); return (int)T.size() - 1; };
-  std::vector<int> stage0(nsig);
-  for (int i = 0; i < nsig; ++i) {
+  auto stage0_task = [&](int i) {
     Task t{};
     t.op = fam ? OP_FAM_CHAN : OP_SSCA_CDP;
     t.size = Np;
@@ -384,11 +389,13 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     t.x_off = p->x_off[i]; t.out_off = p->out_off[i]; t.ws_off = p->ws_off[i];
     if (fam) { t.P = (int)p->sizes[i]; t.tiles = (t.P + cnp - 1) / cnp; }
     else { t.N = (int)p->sizes[i]; t.tiles = t.N / cnp; }
-    stage0[i] = add(t);
-  }
-  for (int i = 0; i < nsig; ++i) {
-    const int64_t sz = p->sizes[i];
-    if (fam) {
+    return t;
+  };
+  std::vector<int> stage0(nsig, -1), cols_idx(nsig, -1);
+  if (fam) {
+    for (int i = 0; i < nsig; ++i) stage0[i] = add(stage0_task(i));
+    for (int i = 0; i < nsig; ++i) {
+      const int64_t sz = p->sizes[i];
       Task t = T[stage0[i]];
       t.op = OP_FAM_PAIRS; t.size = (int)sz; t.dep = stage0[i];
       const int c = tile_c((int)sz);
@@ -396,26 +403,36 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
       if (!(t.tw = table_pass((int)sz, &e))) { free_plan(p); return cuda_status(e); }
       if (tc && !(t.bmats = table_tc_bmats((int)sz, &t.bbytes, &e))) { free_plan(p); return cuda_status(e); }
       add(t);
-    } else {
-      int M1, M2;
-      ssca_split(sz, &M1, &M2);
-      Task c1 = T[stage0[i]];
-      c1.op = OP_SSCA_COLS; c1.size = M1; c1.dep = stage0[i]; c1.M1 = M1; c1.M2 = M2;
-      c1.tiles = (int64_t)Np * (M2 / tile_c(M1));
-      if (!(c1.tw = table_pass(M1, &e)) || !(c1.wN = table_roots((int)sz, &e)) ||
-          !(c1.cols = table_cols((int)sz, M1, tile_c(M1), &e))) {
-        free_plan(p);
-        return cuda_status(e);
+    }
+  } else {
+    for (int s = 0; s < nsig + 2; ++s) {
+      if (s < nsig) stage0[s] = add(stage0_task(s));
+      if (s >= 1 && s - 1 < nsig) {                             // column pass of signal s-1
+        const int i = s - 1;
+        const int64_t sz = p->sizes[i];
+        int M1, M2;
+        ssca_split(sz, &M1, &M2);
+        Task c1 = T[stage0[i]];
+        c1.op = OP_SSCA_COLS; c1.size = M1; c1.dep = stage0[i]; c1.M1 = M1; c1.M2 = M2;
+        c1.tiles = (int64_t)Np * (M2 / tile_c(M1));
+        if (!(c1.tw = table_pass(M1, &e)) || !(c1.wN = table_roots((int)sz, &e)) ||
+            !(c1.cols = table_cols((int)sz, M1, tile_c(M1), &e))) {
+          free_plan(p);
+          return cuda_status(e);
+        }
+        if (tc && !(c1.bmats = table_tc_bmats(M1, &c1.bbytes, &e))) { free_plan(p); return cuda_status(e); }
+        cols_idx[i] = add(c1);
       }
-      if (tc && !(c1.bmats = table_tc_bmats(M1, &c1.bbytes, &e))) { free_plan(p); return cuda_status(e); }
-      const int ci = add(c1);
-      Task r = c1;
-      r.op = OP_SSCA_ROWS; r.size = M2; r.dep = ci;
-      r.tiles = (int64_t)Np * (M1 / tile_c(M2));
-      r.wN = nullptr; r.cols = nullptr; r.bmats = nullptr; r.bbytes = 0;
-      if (!(r.tw = table_pass(M2, &e))) { free_plan(p); return cuda_status(e); }
-      if (tc && !(r.bmats = table_tc_bmats(M2, &r.bbytes, &e))) { free_plan(p); return cuda_status(e); }
-      add(r);
+      if (s >= 2 && s - 2 < nsig) {                             // row pass of signal s-2
+        const int i = s - 2;
+        Task r = T[cols_idx[i]];
+        r.op = OP_SSCA_ROWS; r.size = r.M2; r.dep = cols_idx[i];
+        r.tiles = (int64_t)Np * (r.M1 / tile_c(r.M2));
+        r.wN = nullptr; r.cols = nullptr; r.bmats = nullptr; r.bbytes = 0;
+        if (!(r.tw = table_pass(r.M2, &e))) { free_plan(p); return cuda_status(e); }
+        if (tc && !(r.bmats = table_tc_bmats(r.M2, &r.bbytes, &e))) { free_plan(p); return cuda_status(e); }
+        add(r);
+      }
     }
   }
   p->total = first;

@@ -228,6 +228,27 @@ struct FftPieces {
   }
 };
 
+// ----------------------------------------------------------------------------- team barrier
+// Barrier among the T threads of one transform.  With consecutive threads per transform
+// (!CFAST) a transform of at most 32 threads lives inside one warp (__syncwarp), a larger one
+// occupies whole warps and uses its own named barrier (1 + team index; 0 is __syncthreads),
+// so transforms of one CTA do not wait for each other.  Interleaved transforms (CFAST) span
+// every warp and use the CTA barrier.
+template <int T, bool CFAST>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (CFAST) {
+    __syncthreads();
+  } else if constexpr (T <= 32) {
+    __syncwarp();
+  } else {
+    if (T >= (int)blockDim.x) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" :: "r"(1 + (int)threadIdx.x / T), "r"(T) : "memory");
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- batched FFT
 // C transforms of size M per CTA, T = M/E threads each (blockDim.x == C*T).
 // CFAST: thread tid works on transform c = tid % C (transforms interleaved across lanes,
@@ -255,15 +276,15 @@ __device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2*
     F::template pass_out<0>(c, t, dst, v);
   } else {
     F::pass0_store(t, reg, v);
-    __syncthreads();
+    team_sync<T, CFAST>();
     F::template pass_load<1>(t, reg, tw, v);
     if constexpr (PI::n == 2) {
       if constexpr (SYNC_DST) __syncthreads();
       F::template pass_out<1>(c, t, dst, v);
     } else {
-      __syncthreads();                     // every read of pass 1 precedes its writes
+      team_sync<T, CFAST>();               // every read of pass 1 precedes its writes
       F::template pass_store<1>(t, reg, v);
-      __syncthreads();
+      team_sync<T, CFAST>();
       F::template pass_load<2>(t, reg, tw, v);
       if constexpr (SYNC_DST) __syncthreads();
       F::template pass_out<2>(c, t, dst, v);

@@ -52,17 +52,18 @@ template <int PP, bool TC>
 __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X, int Np,
                                                float2* __restrict__ out, const float2* __restrict__ tw, int64_t pair0) {
   using S = TileShape<PP>;
-  const int64_t npairs = (int64_t)Np * Np;
-  auto src = [&](int c, int p) -> float2 {
-    const int64_t pair = pair0 + c;
-    if (pair >= npairs) return make_float2(0.f, 0.f);
-    const int kh = (int)(pair / Np), lh = (int)(pair % Np);
-    return cmulc(__ldg(X + (int64_t)kh * PP + p), __ldg(X + (int64_t)lh * PP + p));
+  // this thread's pair (transforms are t-fast: c = tid / T), resolved once
+  const int64_t pair = pair0 + (int)threadIdx.x / S::T;
+  const bool valid = pair < (int64_t)Np * Np;
+  const int kh = valid ? (int)(pair / Np) : 0, lh = valid ? (int)(pair % Np) : 0;
+  const float2* __restrict__ xk = X + (int64_t)kh * PP;
+  const float2* __restrict__ xl = X + (int64_t)lh * PP;
+  float2* __restrict__ o = out + pair * PP;
+  auto src = [&](int, int p) -> float2 {
+    return valid ? cmulc(__ldg(xk + p), __ldg(xl + p)) : make_float2(0.f, 0.f);
   };
-  auto dst = [&](int c, int f, float2 v) {
-    const int64_t pair = pair0 + c;
-    if (pair >= npairs) return;
-    out[pair * PP + ((f + PP / 2) & (PP - 1))] = v;
+  auto dst = [&](int, int f, float2 v) {
+    if (valid) o[(f + PP / 2) & (PP - 1)] = v;
   };
   tile_fft<PP, S::C, false, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
@@ -74,17 +75,24 @@ __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const floa
                                               const float* __restrict__ a, const float2* __restrict__ wnp,
                                               const float2* __restrict__ tw, float2* __restrict__ Xg, int n0) {
   using S = TileShape<NP>;
-  auto src = [&](int c, int r) -> float2 {
-    const int m = n0 + c - NP / 2 + r;
-    if (m < 0 || m >= N) return make_float2(0.f, 0.f);
-    return cscale(__ldg(x + m), __ldg(a + r));
+  // this thread's time point (transforms interleaved: c = tid % C), resolved once
+  const int n = n0 + (int)threadIdx.x % S::C;
+  const bool interior = n0 - NP / 2 >= 0 && n0 + S::C + NP / 2 <= N;   // whole tile away from the ends
+  const float2* __restrict__ xb = x + (n - NP / 2);
+  const float2 xn = __ldg(x + n);
+  const int s = (n - NP / 2) & (NP - 1);                            // s mod Np (s may be < 0)
+  float2* __restrict__ o = Xg + n;
+  auto src = [&](int, int r) -> float2 {
+    if (!interior) {
+      const int m = n - NP / 2 + r;
+      if (m < 0 || m >= N) return make_float2(0.f, 0.f);
+    }
+    return cscale(__ldg(xb + r), __ldg(a + r));
   };
-  auto dst = [&](int c, int f, float2 v) {
-    const int n = n0 + c;
-    const int s = (n - NP / 2) & (NP - 1);                        // s mod Np (s may be < 0)
+  auto dst = [&](int, int f, float2 v) {
     const int kh = (f + NP / 2) & (NP - 1);
     const float2 y = cmul(v, __ldg(wnp + ((f * s) & (NP - 1))));
-    Xg[(int64_t)kh * N + n] = cmulc(y, __ldg(x + n));
+    o[(int64_t)kh * N] = cmulc(y, xn);
   };
   tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
@@ -99,10 +107,14 @@ __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const flo
                                                const float2* __restrict__ tw, int m20) {
   using S = TileShape<M1>;
   constexpr int C = S::C;
-  auto src = [&](int c, int m1) -> float2 { return in[(int64_t)m1 * M2 + m20 + c]; };
-  auto dst = [&](int c, int f, float2 v) {
-    const float2 w = cmul(__ldg(wN + ((m20 * f) & (N - 1))), __ldg(cols + f * C + c));  // W_N^{(m20+c) f}
-    out[(int64_t)f * M2 + m20 + c] = cmul(v, w);
+  const int c = (int)threadIdx.x % C;                             // interleaved columns: c = tid % C
+  const float2* ib = in + m20 + c;
+  float2* ob = out + m20 + c;
+  const float2* __restrict__ colc = cols + c;
+  auto src = [&](int, int m1) -> float2 { return ib[(int64_t)m1 * M2]; };
+  auto dst = [&](int, int f, float2 v) {
+    const float2 w = cmul(__ldg(wN + ((m20 * f) & (N - 1))), __ldg(colc + f * C));  // W_N^{(m20+c) f}
+    ob[(int64_t)f * M2] = cmul(v, w);
   };
   tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
@@ -119,8 +131,8 @@ __device__ __forceinline__ void ssca_rows_tile(float2* sm, TcCtx& ctx, const flo
                                                int M1, const float2* __restrict__ tw, int r0) {
   using S = TileShape<M2>;
   constexpr int C = S::C;
-  const float2* rowp = in + (int64_t)r0 * M2;
-  auto src = [&](int c, int m2) -> float2 { return rowp[c * M2 + m2]; };
+  const float2* __restrict__ rowp = in + (int64_t)(r0 + (int)threadIdx.x / S::T) * M2;   // t-fast: c = tid / T
+  auto src = [&](int, int m2) -> float2 { return rowp[m2]; };
   auto dst = [&](int c, int f, float2 v) { sm[f * (C + 1) + c] = v; };
   tile_fft<M2, C, false, true, S::NT, TC>(sm, tw, ctx, src, dst);
   __syncthreads();
