@@ -54,6 +54,15 @@ typedef enum {
 
 typedef enum { SCD_FP32 = 0, SCD_SPLIT_BF16 = 1 } scd_precision;
 
+/* How scd_ssca schedules its stages.
+ * STAGES: one kernel per stage (channeliser + CDP, column pass, row pass).
+ * PERSISTENT: one persistent launch that runs the channeliser + CDP and then the column and
+ *   row passes channel group by channel group through small rotating slots (so each group's
+ *   intermediate is read back from L2).
+ * AUTO: the choice scd_ssca_tune measured fastest for (N, Np, precision) on this GPU model
+ *   (in this process, or from the SCD_TUNE_CACHE file); STAGES if never tuned. */
+typedef enum { SCD_SCHEDULE_AUTO = 0, SCD_SCHEDULE_STAGES = 1, SCD_SCHEDULE_PERSISTENT = 2 } scd_schedule;
+
 /* Options.  Pass NULL for defaults: legacy default stream, FP32, no workspace, |S|,
  * no stage events.  Zero-initialise the struct before filling it. */
 typedef struct {
@@ -66,9 +75,11 @@ typedef struct {
    * least (kernels launched by the call) + 1, event i (a cudaEvent_t, see
    * scd_events_create) is recorded on the stream just before the call's i-th kernel and
    * the next one after its last kernel.  scd_fam launches 2 kernels (channeliser, pair
-   * FFT), scd_ssca 3 (channeliser + CDP, column pass, row pass), each map 1. */
+   * FFT); scd_ssca 3 with the STAGES schedule (channeliser + CDP, column pass, row pass) or 1
+   * with PERSISTENT (AUTO resolves to one of the two); each map 1. */
   void** stage_events;
   int32_t n_stage_events;
+  int32_t schedule;         /* scd_ssca only: scd_schedule */
 } scd_opts;
 
 /* ------------------------------------------------------------------------------ FAM
@@ -163,6 +174,26 @@ SCD_API scd_status scd_batch_run(scd_batch_plan* plan, const void* x_arena, cons
                                  void* workspace, void* stream);
 SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
 
+/* ------------------------------------------------------------------------------ autotuner
+ * The persistent schedule has two sizing knobs: how much output one queue item covers (the
+ * scheduling cost is paid once per item) and, for SSCA, how many channels one unit of the
+ * column/row passes covers (the size of its rotating slot, which decides whether the
+ * intermediate can stay in L2).  The autotuner times candidate settings on the caller's
+ * buffers and keeps the fastest; it records the choice per (GPU model, workload) in this
+ * process and, when the environment variable SCD_TUNE_CACHE names a file, in that JSON file,
+ * from which later processes start.  Both calls enqueue and time real runs on `stream`
+ * (the outputs hold a valid estimate afterwards) and synchronise it.
+ *
+ * scd_batch_tune: items of 32..512 KiB, SSCA slots of 8..64 MiB; re-plans `plan` with the
+ *   fastest setting (plans created later for the same workload start from it).
+ * scd_ssca_tune: the STAGES schedule and the PERSISTENT one with the same knobs, for
+ *   (N, Np, opts->precision); later SCD_SCHEDULE_AUTO calls use the fastest.  Arguments as
+ *   scd_ssca (opts->workspace at least scd_ssca_workspace_bytes). */
+SCD_API scd_status scd_batch_tune(scd_batch_plan* plan, const void* x_arena, const float* window, void* out_arena,
+                                  void* workspace, void* stream, int32_t reps);
+SCD_API scd_status scd_ssca_tune(const void* x, int64_t N, int32_t Np, const float* window, void* out,
+                                 const scd_opts* opts, int32_t reps);
+
 /* ------------------------------------------------------------------------------ host buffers
  * scd_fam_host / scd_ssca_host: the same estimates for HOST input and output buffers
  * (pinned memory gives full copy bandwidth; pageable memory works).  The call copies x
@@ -205,6 +236,8 @@ SCD_API scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t
 SCD_API scd_status scd_events_create(int32_t n, void** events);
 SCD_API scd_status scd_events_destroy(int32_t n, void** events);
 SCD_API scd_status scd_event_elapsed_ms(void* start, void* end, float* ms);
+/* Records one of those events on `stream` (a cudaStream_t). */
+SCD_API scd_status scd_event_record(void* event, void* stream);
 /* Synchronises `stream` and reports whether a kernel of this library on the current
  * device gave up a bounded device-side wait since the last call (SCD_ERR_TIMEOUT; the
  * affected estimate is invalid); clears the record.  SCD_OK otherwise. */

@@ -27,6 +27,7 @@ class ScdOpts(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t),
         ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
         ("n_stage_events", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
     ]
 
 
@@ -53,9 +54,12 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_size_t)]),
     "scd_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "scd_batch_plan_destroy": (None, [_vp]),
+    "scd_batch_tune": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
+    "scd_ssca_tune": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p, _i32]),
     "scd_events_create": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_events_destroy": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_event_elapsed_ms": (_i32, [_vp, _vp, ctypes.POINTER(ctypes.c_float)]),
+    "scd_event_record": (_i32, [_vp, _vp]),
     "scd_check_device": (_i32, [_vp]),
     "scd_launch_count": (ctypes.c_uint64, []),
     "scd_prepare": (_i32, [_i32, _i64, _i32, _i32]),
@@ -125,9 +129,13 @@ def _need(t, dtype, numel, name):
         raise TypeError(f"{name} must be a contiguous {dtype} tensor of at least {numel} elements")
 
 
-def make_opts(stream=None, precision="fp32", workspace=None, map_power=1) -> ScdOpts:
+SCHEDULES = {"auto": 0, "stages": 1, "persistent": 2}
+
+
+def make_opts(stream=None, precision="fp32", workspace=None, map_power=1, schedule="auto") -> ScdOpts:
     o = ScdOpts()
     o.stream = _stream(stream)
+    o.schedule = SCHEDULES[schedule]
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.map_power = int(map_power)
     if workspace is not None:
@@ -161,7 +169,7 @@ def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32",
     return out
 
 
-def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None):
+def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None, schedule="auto"):
     """SSCA estimate of the complex64 CUDA tensor x (N = x.numel()); returns complex64 [Np, N]."""
     torch = _torch()
     lib = load()
@@ -174,7 +182,7 @@ def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, w
     _need(out, torch.complex64, Np * N, "out")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     ws = _workspace(lib.scd_ssca_workspace_bytes(N, Np, prec), x.device, workspace)
-    o = make_opts(stream, prec, ws)
+    o = make_opts(stream, prec, ws, schedule=schedule)
     check(lib.scd_ssca(_ptr(x), N, Np, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_ssca")
     return out
 
@@ -203,6 +211,20 @@ def scd_ssca_map(S, N: int, Np: int, map=None, power: int = 1, stream=None):
     o = make_opts(stream, "fp32", None, power)
     check(lib.scd_ssca_map(_ptr(S), N, Np, _ptr(map), ctypes.byref(o)), "scd_ssca_map")
     return map
+
+
+def scd_ssca_tune(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None, reps=3):
+    """Times scd_ssca's schedules for (N, Np, precision) and keeps the fastest for "auto"."""
+    torch = _torch()
+    lib = load()
+    N = x.numel()
+    if out is None:
+        out = torch.empty((Np, N), dtype=torch.complex64, device=x.device)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    ws = _workspace(lib.scd_ssca_workspace_bytes(N, Np, prec), x.device, workspace)
+    o = make_opts(stream, prec, ws)
+    check(lib.scd_ssca_tune(_ptr(x), N, Np, _ptr(window), _ptr(out), ctypes.byref(o), reps), "scd_ssca_tune")
+    return out
 
 
 def scd_check_device(stream=None) -> None:
@@ -248,6 +270,12 @@ class BatchPlan:
         _need(out_arena, torch.complex64, self.out_offsets[-1], "out_arena")
         check(self.lib.scd_batch_run(self.handle, _ptr(x_arena), _ptr(window), _ptr(out_arena),
                                      _ptr(workspace), _stream(stream)), "scd_batch_run")
+
+    def tune(self, x_arena, out_arena, workspace, window=None, stream=None, reps=3):
+        """Times the persistent schedule's sizing candidates on these buffers, keeps the fastest
+        (scd_batch_tune); the output holds a valid estimate afterwards."""
+        check(self.lib.scd_batch_tune(self.handle, _ptr(x_arena), _ptr(window), _ptr(out_arena), _ptr(workspace),
+                                      _stream(stream), reps), "scd_batch_tune")
 
     def output(self, out_arena, i):
         """View of signal i's estimate in the output arena."""

@@ -24,7 +24,7 @@ scd_status cuda_fail(cudaError_t e) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-const scd_opts kDefaultOpts = {nullptr, SCD_FP32, 1, nullptr, 0, nullptr, 0};
+const scd_opts kDefaultOpts = {nullptr, SCD_FP32, 1, nullptr, 0, nullptr, 0, SCD_SCHEDULE_AUTO};
 
 // Records opts.stage_events[i] (when the caller asked for at least `needed` events).
 struct StageMarks {
@@ -80,7 +80,8 @@ size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t P, int3
 size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision) {
   (void)precision;
   if (Np < 1 || N < 1) return 0;
-  return round_up(sizeof(float) * 2 * (size_t)Np * (size_t)N, 256);   // X_g / column-pass output
+  // the persistent schedule's X_g + rotating slots + counters cover the staged schedule's X_g
+  return scd::ssca_persistent_workspace(N, Np);
 }
 
 scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window, void* out,
@@ -123,6 +124,22 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
     if (!window) return cuda_fail(e);
   }
   float2* ws = (float2*)o.workspace;
+  scd::TuneEntry choice{o.schedule, 0, 0, 0.0};
+  if (o.schedule == SCD_SCHEDULE_AUTO) choice = scd::ssca_auto_choice(N, Np, o.precision);
+  if (choice.schedule != SCD_SCHEDULE_STAGES && choice.schedule != SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
+  if (choice.schedule == SCD_SCHEDULE_PERSISTENT) {
+    StageMarks m{o, 2};
+    if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
+    scd_status r = choice.item_bytes
+                       ? scd::ssca_persistent_tuned((const float2*)x, N, Np, window, (float2*)out, o.workspace,
+                                                    o.workspace_bytes, st, o.precision, choice.item_bytes,
+                                                    choice.slot_bytes)
+                       : scd::ssca_persistent((const float2*)x, N, Np, window, (float2*)out, o.workspace,
+                                              o.workspace_bytes, st, o.precision);
+    if (r != SCD_OK) return r;
+    if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
+    return SCD_OK;
+  }
   StageMarks m{o, 4};
   if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
   if ((e = scd::ssca_cdp((const float2*)x, N, Np, window, ws, st, o.precision)) != cudaSuccess) return cuda_fail(e);
@@ -288,6 +305,12 @@ scd_status scd_event_elapsed_ms(void* start, void* end, float* ms) {
   return e == cudaSuccess ? SCD_OK : cuda_fail(e);
 }
 
+scd_status scd_event_record(void* event, void* stream) {
+  if (!event) return SCD_ERR_ARG;
+  cudaError_t e = cudaEventRecord((cudaEvent_t)event, (cudaStream_t)stream);
+  return e == cudaSuccess ? SCD_OK : cuda_fail(e);
+}
+
 scd_status scd_check_device(void* stream) {
   cudaError_t e;
   unsigned* w = scd::device_error_word(&e);
@@ -303,7 +326,10 @@ scd_status scd_check_device(void* stream) {
 
 uint64_t scd_launch_count(void) { return scd::g_launches.load(std::memory_order_relaxed); }
 
-void scd_release_cache(void) { scd::release_tables(); }
+void scd_release_cache(void) {
+  scd::release_single_plans();
+  scd::release_tables();
+}
 
 const char* scd_status_string(scd_status s) {
   switch (s) {

@@ -17,6 +17,7 @@
 // samples beyond those are not used.
 #include <stdio.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -32,8 +33,12 @@ enum Op : int32_t { OP_FAM_CHAN = 0, OP_FAM_PAIRS = 1, OP_SSCA_CDP = 2, OP_SSCA_
 
 struct Task {
   int32_t op, size, dep, bbytes;          // op, transform size, prerequisite task (-1), B bytes
-  int64_t first, tiles;                   // tile range [first, first + tiles)
+  int32_t dep2, ch0;                      // second prerequisite (-1); SSCA: first channel of the unit
+  int64_t first, tiles;                   // queue items [first, first + tiles)
+  int64_t subtiles;                       // CTA tiles of the task; one queue item covers `per_item`
+  int32_t per_item, pad_;
   int64_t x_off, out_off, ws_off;         // element offsets into the arenas
+  int64_t mid_off;                        // SSCA: workspace offset of the unit's column-pass slot
   int32_t N, P, M1, M2;                   // the signal's sizes
   const float2* tw;                       // pass twiddles of this task's transform size
   const float2* wN;                       // SSCA column pass: W_N^j
@@ -58,6 +63,17 @@ struct BatchArgs {
 };
 
 constexpr int kThreads = 256;
+constexpr int kSlots = 3;                                  // rotating column-pass slots (SSCA)
+constexpr int64_t kSlotBytes = 16ll << 20;                 // target bytes of one slot
+constexpr int64_t kItemBytes = 128ll << 10;                // output bytes per queue item (target)
+constexpr int64_t kSlotBytesMax = 64ll << 20;              // largest slot the autotuner tries
+
+// Channels per SSCA unit: the largest power of two G <= Np with G N 8 <= slot bytes.
+int64_t slot_group(int Np, int64_t N, int64_t slot_bytes) {
+  int64_t G = Np;
+  while (G > 1 && G * N * 8 > slot_bytes) G >>= 1;
+  return G;
+}
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bound on any dependency wait
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -154,14 +170,16 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
 #undef SCD_CD
     }
   } else if (t.op == OP_SSCA_COLS) {
+    // unit of channels [ch0, ch0 + G): X_g rows of the signal -> the unit's slot
     load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
     switch (t.M1) {
 #define SCD_CO(MV)                                                                          \
   case MV: {                                                                                \
     constexpr int C = TileShape<MV>::C;                                                     \
     const int per = t.M2 / C;                                                               \
-    float2* row = ws + (int64_t)(tile / per) * t.N;                                         \
-    ssca_cols_tile<MV, TC>(sm, ctx, row, row, t.N, t.M2, t.wN, t.cols, t.tw, (int)(tile % per) * C); \
+    const int64_t kh = tile / per;                                                          \
+    ssca_cols_tile<MV, TC>(sm, ctx, ws + (t.ch0 + kh) * t.N, A.ws + t.mid_off + kh * t.N, t.N, t.M2, t.wN, \
+                           t.cols, t.tw, (int)(tile % per) * C);                            \
   } break;
       SCD_CO(64) SCD_CO(128) SCD_CO(256) SCD_CO(512) SCD_CO(1024)
 #undef SCD_CO
@@ -175,7 +193,8 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
     constexpr int C = TileShape<MV>::C;                                                     \
     const int per = t.M1 / C;                                                               \
     const int64_t kh = tile / per;                                                          \
-    ssca_rows_tile<MV, TC>(sm, ctx, ws + kh * t.N, out + kh * t.N, t.M1, t.tw, (int)(tile % per) * C); \
+    ssca_rows_tile<MV, TC>(sm, ctx, A.ws + t.mid_off + kh * t.N, out + (t.ch0 + kh) * t.N, t.M1, t.tw, \
+                           (int)(tile % per) * C);                                          \
   } break;
       SCD_RO(64) SCD_RO(128) SCD_RO(256) SCD_RO(512) SCD_RO(1024)
 #undef SCD_RO
@@ -210,17 +229,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs A) {
       if (tile < A.total) {
         next = (int64_t)atomicAdd(A.counters, 1u);           // claim the following tile now
         while (cur + 1 < A.ntasks && __ldg(&A.tasks[cur + 1].first) <= tile) ++cur;
-        const int dep = __ldg(&A.tasks[cur].dep);
-        if (dep >= 0 && dep_ok_task != cur) {
-          const unsigned need = (unsigned)__ldg(&A.tasks[dep].tiles);
+        if (dep_ok_task != cur) {
+          const int deps[2] = {__ldg(&A.tasks[cur].dep), __ldg(&A.tasks[cur].dep2)};
           const unsigned long long t0 = globaltimer();
-          while (ld_acquire(A.counters + 1 + dep) < need) {
-            if (globaltimer() - t0 > kWaitNs) {
-              atomicOr(A.err, 2u);
-              skip = 1;
-              break;
+          for (int d = 0; d < 2 && !skip; ++d) {
+            if (deps[d] < 0) continue;
+            const unsigned need = (unsigned)__ldg(&A.tasks[deps[d]].tiles);
+            while (ld_acquire(A.counters + 1 + deps[d]) < need) {
+              if (globaltimer() - t0 > kWaitNs) {
+                atomicOr(A.err, 2u);
+                skip = 1;
+                break;
+              }
+              __nanosleep(128);
             }
-            __nanosleep(128);
           }
           if (!skip) dep_ok_task = cur;
         }
@@ -233,8 +255,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs A) {
     if (tile >= A.total) break;
     const Task& t = A.tasks[s_task];
     if (!s_skip) {
-      if constexpr (FAM) fam_tile<TC>(A, t, tile - t.first, sm, ctx, bsm, loaded);
-      else ssca_tile<TC>(A, t, tile - t.first, sm, ctx, bsm, loaded);
+      const int64_t s0 = (tile - t.first) * t.per_item;
+      const int64_t s1 = s0 + t.per_item < t.subtiles ? s0 + t.per_item : t.subtiles;
+      for (int64_t st = s0; st < s1; ++st) {
+        if (st > s0) __syncthreads();                        // shared memory reused by the next tile
+        if constexpr (FAM) fam_tile<TC>(A, t, st, sm, ctx, bsm, loaded);
+        else ssca_tile<TC>(A, t, st, sm, ctx, bsm, loaded);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -286,6 +313,9 @@ int tile_c(int M) {                       // transforms per tile for size M (256
 
 struct scd_batch_plan {
   int estimator = 0, nsig = 0, Np = 0, L = 0, precision = 0, device = 0;
+  int64_t item_bytes = scd::kItemBytes;   // tunables (autotuner): output bytes per queue item,
+  int64_t slot_bytes = scd::kSlotBytes;   // bytes of one SSCA column-pass slot
+  uint64_t signature = 0;                 // hash of (estimator, Np, L, precision, lengths)
   std::vector<int64_t> x_off, out_off, ws_off, sizes, used;
   std::vector<scd::Task> tasks;
   scd::Task* d_tasks = nullptr;
@@ -323,6 +353,169 @@ scd_status cuda_status(cudaError_t e) {
   snprintf(msg, sizeof msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   scd::set_last_error(msg);
   return SCD_ERR_CUDA;
+}
+
+// (Re)builds the plan's task list with its current tunables and uploads it.
+scd_status build_tasks(scd_batch_plan* p) {
+  using namespace scd;
+  const int nsig = p->nsig, Np = p->Np;
+  const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
+  cudaError_t e = cudaSuccess;
+  p->tasks.clear();
+  p->ws_bytes = sizeof(float2) * (size_t)p->ws_off[nsig];
+  // Task order.  FAM: every channeliser task (tiny), then every pair task.  SSCA: software-
+  // pipelined by signal (cdp_s, cols_{s-1}, rows_{s-2}, ...), so a signal's intermediate is
+  // consumed soon after it is produced (small signals stay in L2) and every dependency has
+  // another task queued between it and its consumer.
+  const int cnp = tile_c(Np);
+  std::vector<Task>& T = p->tasks;
+  int64_t first = 0;
+  // One queue item covers enough CTA tiles (of one task) for about kItemBytes of output, so
+  // the scheduling cost (one atomic, a barrier) is spread over several tiles.
+  auto add = [&](Task t) {
+    const int64_t out_per_tile = t.op == OP_FAM_CHAN || t.op == OP_SSCA_CDP
+                                     ? (int64_t)tile_c(Np) * Np * 8
+                                     : (int64_t)tile_c(t.size) * t.size * 8;
+    t.subtiles = t.tiles;
+    t.per_item = (int32_t)std::max<int64_t>(1, p->item_bytes / std::max<int64_t>(1, out_per_tile));
+    t.tiles = (t.subtiles + t.per_item - 1) / t.per_item;
+    t.first = first;
+    first += t.tiles;
+    T.push_back(t);
+    return (int)T.size() - 1;
+  };
+  auto stage0_task = [&](int i) {
+    Task t{};
+    t.op = fam ? OP_FAM_CHAN : OP_SSCA_CDP;
+    t.size = Np;
+    t.dep = -1;
+    t.dep2 = -1;
+    t.x_off = p->x_off[i]; t.out_off = p->out_off[i]; t.ws_off = p->ws_off[i];
+    if (fam) { t.P = (int)p->sizes[i]; t.tiles = (t.P + cnp - 1) / cnp; }
+    else { t.N = (int)p->sizes[i]; t.tiles = t.N / cnp; }
+    return t;
+  };
+  std::vector<int> stage0(nsig, -1), cols_idx(nsig, -1);
+  if (fam) {
+    for (int i = 0; i < nsig; ++i) stage0[i] = add(stage0_task(i));
+    for (int i = 0; i < nsig; ++i) {
+      const int64_t sz = p->sizes[i];
+      Task t = T[stage0[i]];
+      t.op = OP_FAM_PAIRS; t.size = (int)sz; t.dep = stage0[i];
+      const int c = tile_c((int)sz);
+      t.tiles = ((int64_t)Np * Np + c - 1) / c;
+      if (!(t.tw = table_pass((int)sz, &e))) { return cuda_status(e); }
+      if (tc && !(t.bmats = table_tc_bmats((int)sz, &t.bbytes, &e))) { return cuda_status(e); }
+      add(t);
+    }
+  } else {
+    // SSCA: the column and row passes run per unit of G channels of one signal; a unit's
+    // column-pass output goes to one of kSlots rotating slots of G*N values and is read by
+    // the unit's row pass right away, so it can stay in L2.  Order: cdp_0, then per signal s:
+    // cdp_{s+1}, then (cols_u, rows_u) for the units of s.  cols_u waits for the signal's cdp
+    // and for rows_{u - kSlots} (the previous user of its slot).
+    std::vector<int> rows_task;                                 // per unit, in order
+    auto units_of = [&](int64_t N) {
+      int G = Np;
+      while (G > 1 && (int64_t)G * N * 8 > p->slot_bytes) G >>= 1;
+      return G;
+    };
+    int64_t slot_elems = 0;                                     // sized for the largest tunable slot
+    for (int i = 0; i < nsig; ++i) slot_elems = std::max<int64_t>(slot_elems, slot_group(Np, p->sizes[i], kSlotBytesMax) * p->sizes[i]);
+    const int64_t slots_off = p->ws_off[nsig];
+    p->ws_bytes = sizeof(float2) * (size_t)(slots_off + kSlots * slot_elems);
+    // units in signal order; rows passes lag the column passes by one unit so that no row
+    // pass is queued right behind the column pass it waits for
+    struct Unit { int sig, ch0, G; };
+    std::vector<Unit> units;
+    for (int i = 0; i < nsig; ++i) {
+      const int G = units_of(p->sizes[i]);
+      for (int g = 0; g < Np / G; ++g) units.push_back({i, g * G, G});
+    }
+    const int U = (int)units.size();
+    std::vector<Task> cols_t(U), rows_t(U);
+    std::vector<int> cols_idx(U, -1);
+    rows_task.assign(U, -1);
+    for (int u = 0; u < U; ++u) {
+      const int i = units[u].sig, G = units[u].G;
+      const int64_t sz = p->sizes[i];
+      int M1, M2;
+      ssca_split(sz, &M1, &M2);
+      Task c1 = stage0_task(i);
+      c1.op = OP_SSCA_COLS; c1.size = M1; c1.M1 = M1; c1.M2 = M2; c1.ch0 = units[u].ch0;
+      c1.tiles = (int64_t)G * (M2 / tile_c(M1));
+      c1.mid_off = slots_off + (int64_t)(u % kSlots) * slot_elems;
+      if (!(c1.tw = table_pass(M1, &e)) || !(c1.wN = table_roots((int)sz, &e)) ||
+          !(c1.cols = table_cols((int)sz, M1, tile_c(M1), &e)))
+        return cuda_status(e);
+      if (tc && !(c1.bmats = table_tc_bmats(M1, &c1.bbytes, &e))) { return cuda_status(e); }
+      Task r = c1;
+      r.op = OP_SSCA_ROWS; r.size = M2;
+      r.tiles = (int64_t)G * (M1 / tile_c(M2));
+      r.wN = nullptr; r.cols = nullptr; r.bmats = nullptr; r.bbytes = 0;
+      if (!(r.tw = table_pass(M2, &e))) { return cuda_status(e); }
+      if (tc && !(r.bmats = table_tc_bmats(M2, &r.bbytes, &e))) { return cuda_status(e); }
+      cols_t[u] = c1;
+      rows_t[u] = r;
+    }
+    int next_cdp = 0;
+    auto emit_cdp = [&]() { stage0[next_cdp] = add(stage0_task(next_cdp)); ++next_cdp; };
+    if (nsig > 0) emit_cdp();
+    for (int j = 0; j <= U; ++j) {
+      if (j < U) {
+        const int i = units[j].sig;
+        if (next_cdp == i + 1 && next_cdp < nsig) emit_cdp();     // one signal's channeliser ahead
+        Task c1 = cols_t[j];
+        c1.dep = stage0[i];
+        c1.dep2 = j >= kSlots ? rows_task[j - kSlots] : -1;    // previous user of the slot
+        cols_idx[j] = add(c1);
+      }
+      if (j >= 1) {
+        Task r = rows_t[j - 1];
+        r.dep = cols_idx[j - 1];
+        r.dep2 = -1;
+        rows_task[j - 1] = add(r);
+      }
+    }
+  }
+  p->total = first;
+  if (p->total >= (int64_t)0xFFFFFFF0u) return SCD_ERR_UNSUPPORTED;
+  if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+  if (p->d_tasks) { cudaFree(p->d_tasks); p->d_tasks = nullptr; }
+  if (p->d_counters) { cudaFree(p->d_counters); p->d_counters = nullptr; }
+  if ((e = cudaMalloc(&p->d_tasks, sizeof(Task) * T.size())) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_tasks, T.data(), sizeof(Task) * T.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_counters, sizeof(unsigned) * (T.size() + 1))) != cudaSuccess)
+    return cuda_status(e);
+  return SCD_OK;
+}
+
+std::string batch_key(const scd_batch_plan* p) {
+  char buf[128];
+  snprintf(buf, sizeof buf, "|batch|est=%d|Np=%d|L=%d|p=%d|n=%d|h=%016llx", p->estimator, p->Np, p->L, p->precision,
+           p->nsig, (unsigned long long)p->signature);
+  return scd::device_key() + buf;
+}
+
+// Times `run` (already enqueued work of one candidate) on the stream: one warm-up, then reps.
+template <class Run>
+scd_status time_candidate(cudaStream_t st, int reps, Run run, float* ms) {
+  cudaEvent_t a, b;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return cuda_status(e); }
+  scd_status s = run();
+  if (s == SCD_OK) {
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps && s == SCD_OK; ++r) s = run();
+    cudaEventRecord(b, st);
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) s = cuda_status(e);
+    else if ((e = cudaEventElapsedTime(ms, a, b)) != cudaSuccess) s = cuda_status(e);
+    else *ms /= reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return s;
 }
 
 }  // namespace
@@ -365,7 +558,6 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     p->out_off[i + 1] = p->out_off[i] + outn;
     p->ws_off[i + 1] = p->ws_off[i] + (int64_t)Np * sz;
   }
-  p->ws_bytes = sizeof(float2) * (size_t)p->ws_off[nsig];
   // tables
   if (!(p->wnp = table_roots(Np, &e)) || !(p->tw_np = table_pass(Np, &e)) || !(p->hamming = table_hamming(Np, &e)) ||
       !(p->err = device_error_word(&e))) {
@@ -373,75 +565,16 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     return cuda_status(e);
   }
   if (tc && !(p->bm_np = table_tc_bmats(Np, &p->bbytes_np, &e))) { free_plan(p); return cuda_status(e); }
-  // Task order.  FAM: every channeliser task (tiny), then every pair task.  SSCA: software-
-  // pipelined by signal (cdp_s, cols_{s-1}, rows_{s-2}, ...), so a signal's intermediate is
-  // consumed soon after it is produced (small signals stay in L2) and every dependency has
-  // another task queued between it and its consumer.
-  const int cnp = tile_c(Np);
-  std::vector<Task>& T = p->tasks;
-  int64_t first = 0;
-  auto add = [&](Task t) { t.first = first; first += t.tiles; T.push_back(t); return (int)T.size() - 1; };
-  auto stage0_task = [&](int i) {
-    Task t{};
-    t.op = fam ? OP_FAM_CHAN : OP_SSCA_CDP;
-    t.size = Np;
-    t.dep = -1;
-    t.x_off = p->x_off[i]; t.out_off = p->out_off[i]; t.ws_off = p->ws_off[i];
-    if (fam) { t.P = (int)p->sizes[i]; t.tiles = (t.P + cnp - 1) / cnp; }
-    else { t.N = (int)p->sizes[i]; t.tiles = t.N / cnp; }
-    return t;
-  };
-  std::vector<int> stage0(nsig, -1), cols_idx(nsig, -1);
-  if (fam) {
-    for (int i = 0; i < nsig; ++i) stage0[i] = add(stage0_task(i));
-    for (int i = 0; i < nsig; ++i) {
-      const int64_t sz = p->sizes[i];
-      Task t = T[stage0[i]];
-      t.op = OP_FAM_PAIRS; t.size = (int)sz; t.dep = stage0[i];
-      const int c = tile_c((int)sz);
-      t.tiles = ((int64_t)Np * Np + c - 1) / c;
-      if (!(t.tw = table_pass((int)sz, &e))) { free_plan(p); return cuda_status(e); }
-      if (tc && !(t.bmats = table_tc_bmats((int)sz, &t.bbytes, &e))) { free_plan(p); return cuda_status(e); }
-      add(t);
-    }
-  } else {
-    for (int s = 0; s < nsig + 2; ++s) {
-      if (s < nsig) stage0[s] = add(stage0_task(s));
-      if (s >= 1 && s - 1 < nsig) {                             // column pass of signal s-1
-        const int i = s - 1;
-        const int64_t sz = p->sizes[i];
-        int M1, M2;
-        ssca_split(sz, &M1, &M2);
-        Task c1 = T[stage0[i]];
-        c1.op = OP_SSCA_COLS; c1.size = M1; c1.dep = stage0[i]; c1.M1 = M1; c1.M2 = M2;
-        c1.tiles = (int64_t)Np * (M2 / tile_c(M1));
-        if (!(c1.tw = table_pass(M1, &e)) || !(c1.wN = table_roots((int)sz, &e)) ||
-            !(c1.cols = table_cols((int)sz, M1, tile_c(M1), &e))) {
-          free_plan(p);
-          return cuda_status(e);
-        }
-        if (tc && !(c1.bmats = table_tc_bmats(M1, &c1.bbytes, &e))) { free_plan(p); return cuda_status(e); }
-        cols_idx[i] = add(c1);
-      }
-      if (s >= 2 && s - 2 < nsig) {                             // row pass of signal s-2
-        const int i = s - 2;
-        Task r = T[cols_idx[i]];
-        r.op = OP_SSCA_ROWS; r.size = r.M2; r.dep = cols_idx[i];
-        r.tiles = (int64_t)Np * (r.M1 / tile_c(r.M2));
-        r.wN = nullptr; r.cols = nullptr; r.bmats = nullptr; r.bbytes = 0;
-        if (!(r.tw = table_pass(r.M2, &e))) { free_plan(p); return cuda_status(e); }
-        if (tc && !(r.bmats = table_tc_bmats(r.M2, &r.bbytes, &e))) { free_plan(p); return cuda_status(e); }
-        add(r);
-      }
-    }
-  }
-  p->total = first;
-  if (p->total >= (int64_t)0xFFFFFFF0u) { free_plan(p); return SCD_ERR_UNSUPPORTED; }
-  if ((e = cudaMalloc(&p->d_tasks, sizeof(Task) * T.size())) != cudaSuccess ||
-      (e = cudaMemcpy(p->d_tasks, T.data(), sizeof(Task) * T.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_counters, sizeof(unsigned) * (T.size() + 1))) != cudaSuccess) {
-    free_plan(p);
-    return cuda_status(e);
+  {
+    uint64_t h = 1469598103934665603ull;                       // FNV-1a over the workload
+    auto mix = [&](int64_t v) { for (int b = 0; b < 8; ++b) { h ^= (uint64_t)((v >> (8 * b)) & 0xFF); h *= 1099511628211ull; } };
+    mix(estimator); mix(Np); mix(L); mix(precision); mix(nsig);
+    for (int i = 0; i < nsig; ++i) mix(lengths[i]);
+    p->signature = h;
+    TuneEntry te;
+    if (tune_lookup(batch_key(p), &te)) { p->item_bytes = te.item_bytes; p->slot_bytes = te.slot_bytes; }
+    scd_status bs = build_tasks(p);
+    if (bs != SCD_OK) { free_plan(p); return bs; }
   }
   p->smem = smem_of(fam, tc);
   int per_sm = 0;
@@ -520,4 +653,157 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
 
 void scd_batch_plan_destroy(scd_batch_plan* p) { free_plan(p); }
 
+scd_status scd_batch_tune(scd_batch_plan* p, const void* x_arena, const float* window, void* out_arena,
+                          void* workspace, void* stream, int32_t reps) {
+  using namespace scd;
+  if (!p || reps < 1) return SCD_ERR_ARG;
+  const int64_t items[] = {32ll << 10, 64ll << 10, 128ll << 10, 256ll << 10, 512ll << 10};
+  const int64_t slots[] = {8ll << 20, 16ll << 20, 32ll << 20, 64ll << 20};
+  const int nslots = p->estimator == 0 ? 1 : 4;
+  cudaStream_t st = (cudaStream_t)stream;
+  float best = 3.4e38f;
+  int64_t best_item = p->item_bytes, best_slot = p->slot_bytes;
+  for (int64_t item : items) {
+    for (int k = 0; k < nslots; ++k) {
+      p->item_bytes = item;
+      if (p->estimator == 1) p->slot_bytes = slots[k];
+      scd_status s = build_tasks(p);
+      if (s != SCD_OK) return s;
+      float ms = 0.f;
+      s = time_candidate(st, reps, [&]() { return scd_batch_run(p, x_arena, window, out_arena, workspace, stream); }, &ms);
+      if (s != SCD_OK) return s;
+      if (ms < best) { best = ms; best_item = p->item_bytes; best_slot = p->slot_bytes; }
+    }
+  }
+  p->item_bytes = best_item;
+  p->slot_bytes = best_slot;
+  scd_status s = build_tasks(p);
+  if (s != SCD_OK) return s;
+  tune_store(batch_key(p), TuneEntry{0, best_item, best_slot, best});
+  s = scd_batch_run(p, x_arena, window, out_arena, workspace, stream);   // leave a valid estimate
+  if (s != SCD_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
+}
+
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- single SSCA
+// scd_ssca's default schedule: the whole estimate (channeliser + CDP, then the column and row
+// passes unit by unit through rotating slots) in one persistent launch of the same kernel,
+// from a one-signal plan cached per (device, N, Np, precision).  The tile counters live in
+// the caller's workspace, so concurrent calls with different workspaces do not interfere.
+namespace scd {
+namespace {
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int64_t, int, int, int64_t, int64_t>, scd_batch_plan*> g_plans;
+
+scd_batch_plan* single_plan(int64_t N, int Np, int precision, int64_t item, int64_t slot, cudaError_t* err,
+                            scd_status* st) {
+  int dev = 0;
+  if ((*err = cudaGetDevice(&dev)) != cudaSuccess) { *st = SCD_ERR_CUDA; return nullptr; }
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  auto key = std::make_tuple(dev, N, Np, precision, item, slot);
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) return it->second;
+  scd_batch_plan* p = nullptr;
+  const int64_t len = N;
+  *st = scd_batch_plan_create(1, 1, &len, Np, 1, precision, &p);
+  if (*st != SCD_OK) return nullptr;
+  if (p->item_bytes != item || p->slot_bytes != slot) {
+    p->item_bytes = item;
+    p->slot_bytes = slot;
+    if ((*st = build_tasks(p)) != SCD_OK) { free_plan(p); return nullptr; }
+  }
+  g_plans[key] = p;
+  return p;
+}
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+std::string ssca_key(int64_t N, int Np, int precision) {
+  char buf[96];
+  snprintf(buf, sizeof buf, "|ssca|N=%lld|Np=%d|p=%d", (long long)N, Np, precision);
+  return device_key() + buf;
+}
+}  // namespace
+
+size_t ssca_persistent_workspace(int64_t N, int Np) {
+  const int64_t Gmax = slot_group(Np, N, kSlotBytesMax);
+  const size_t data = sizeof(float2) * (size_t)(Np * N + kSlots * Gmax * N);
+  const size_t ntasks = 1 + 2 * (size_t)Np;                    // at most Np units
+  return up256(data) + up256(sizeof(unsigned) * (ntasks + 1));
+}
+
+scd_status ssca_persistent_tuned(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
+                                 size_t ws_bytes, cudaStream_t st, int precision, int64_t item_bytes,
+                                 int64_t slot_bytes) {
+  cudaError_t e = cudaSuccess;
+  scd_status s = SCD_OK;
+  scd_batch_plan* p = single_plan(N, Np, precision, item_bytes, slot_bytes, &e, &s);
+  if (!p) {
+    if (s == SCD_ERR_CUDA) return cuda_status(e);
+    return s;
+  }
+  const size_t data = up256(p->ws_bytes);
+  const size_t cbytes = sizeof(unsigned) * (p->tasks.size() + 1);
+  if (ws_bytes < data + up256(cbytes)) return SCD_ERR_WORKSPACE;
+  unsigned* counters = (unsigned*)((char*)ws + data);
+  BatchArgs A;
+  A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = Np; A.L = 1; A.total = p->total;
+  A.counters = counters; A.x = x; A.out = out; A.ws = (float2*)ws;
+  A.window = window ? window : p->hamming; A.wnp = p->wnp; A.tw_np = p->tw_np; A.bmats_np = p->bm_np;
+  A.bbytes_np = p->bbytes_np; A.err = p->err;
+  count_launches(1);
+  if ((e = cudaMemsetAsync(counters, 0, cbytes, st)) != cudaSuccess) return cuda_status(e);
+  e = launch_batch(false, precision == SCD_SPLIT_BF16, p->grid, p->smem, A, st);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
+}
+
+scd_status ssca_persistent(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
+                           size_t ws_bytes, cudaStream_t st, int precision) {
+  return ssca_persistent_tuned(x, N, Np, window, out, ws, ws_bytes, st, precision, kItemBytes, kSlotBytes);
+}
+
+TuneEntry ssca_auto_choice(int64_t N, int Np, int precision) {
+  TuneEntry e;
+  if (tune_lookup(ssca_key(N, Np, precision), &e)) return e;
+  return TuneEntry{SCD_SCHEDULE_STAGES, kItemBytes, kSlotBytes, 0.0};
+}
+
+void release_single_plans() {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  for (auto& kv : g_plans) free_plan(kv.second);
+  g_plans.clear();
+}
+
+}  // namespace scd
+
+extern "C" scd_status scd_ssca_tune(const void* x, int64_t N, int32_t Np, const float* window, void* out,
+                                    const scd_opts* opts, int32_t reps) {
+  using namespace scd;
+  if (!opts || reps < 1) return SCD_ERR_ARG;
+  scd_opts o = *opts;
+  o.stage_events = nullptr;
+  o.n_stage_events = 0;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  TuneEntry best{SCD_SCHEDULE_STAGES, kItemBytes, kSlotBytes, 3.4e38};
+  o.schedule = SCD_SCHEDULE_STAGES;
+  float ms = 0.f;
+  scd_status s = time_candidate(st, reps, [&]() { return scd_ssca(x, N, Np, window, out, &o); }, &ms);
+  if (s != SCD_OK) return s;
+  best.ms = ms;
+  const int64_t items[] = {64ll << 10, 128ll << 10, 256ll << 10};
+  const int64_t slots[] = {8ll << 20, 16ll << 20, 32ll << 20, 64ll << 20};
+  for (int64_t item : items)
+    for (int64_t slot : slots) {
+      s = time_candidate(st, reps, [&]() {
+        return ssca_persistent_tuned((const float2*)x, N, Np, window, (float2*)out, o.workspace, o.workspace_bytes, st,
+                                     o.precision, item, slot);
+      }, &ms);
+      if (s != SCD_OK) return s;
+      if (ms < best.ms) best = TuneEntry{SCD_SCHEDULE_PERSISTENT, item, slot, ms};
+    }
+  tune_store(ssca_key(N, Np, o.precision), best);
+  return SCD_OK;
+}

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/scd.h"
 
 namespace scd {
@@ -52,9 +54,31 @@ cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st, int precis
 // Stage 2: M2-point row FFTs, fftshifted into out[kh][sh]
 cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st, int precision);
 
+// Default schedule of scd_ssca: one persistent launch (batch.cu) over a cached one-signal plan.
+size_t ssca_persistent_workspace(int64_t N, int Np);
+scd_status ssca_persistent(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
+                           size_t ws_bytes, cudaStream_t st, int precision);
+void release_single_plans();
+
 // ---------------------------------------------------------------- maps (map.cu)
 cudaError_t fam_map(const float2* S, int Np, int L, int P, int power, float* map, cudaStream_t st);
 cudaError_t ssca_map(const float2* S, int64_t N, int Np, int power, float* map, cudaStream_t st);
+
+// ---------------------------------------------------------------- autotuner cache (tune.cu)
+struct TuneEntry {
+  int schedule;           // scd_schedule for single SSCA calls; 0 for batch plans
+  int64_t item_bytes;     // output bytes per persistent-queue item
+  int64_t slot_bytes;     // bytes of one SSCA column-pass slot
+  double ms;              // measured time of the choice
+};
+std::string device_key();                                    // "<GPU name>/sm<cc>"
+bool tune_lookup(const std::string& key, TuneEntry* out);
+void tune_store(const std::string& key, const TuneEntry& e);
+// scd_ssca under SCD_SCHEDULE_AUTO: the tuned choice, else the default (STAGES)
+TuneEntry ssca_auto_choice(int64_t N, int Np, int precision);
+scd_status ssca_persistent_tuned(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
+                                 size_t ws_bytes, cudaStream_t st, int precision, int64_t item_bytes,
+                                 int64_t slot_bytes);
 
 // ---------------------------------------------------------------- launch accounting
 void count_launches(int n);

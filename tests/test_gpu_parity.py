@@ -82,14 +82,16 @@ def test_fam_paper_scale_sampled_pairs(torch):
 
 
 # ----------------------------------------------------------------------------- SSCA
+@pytest.mark.parametrize("schedule", ["auto", "stages"])
 @pytest.mark.parametrize("N,Np", [
     (1 << 12, 16), (1 << 12, 256), (1 << 13, 32), (1 << 14, 64), (1 << 15, 128), (1 << 17, 32),
 ])
-def test_ssca_matches_oracle(torch, N, Np):
+def test_ssca_matches_oracle(torch, N, Np, schedule):
     x = signals.modulated("qpsk", N, 4, 0.1, 5.0, seed=2000 + Np)
     a = orc.hamming_window(Np)
     ref = orc.ssca(x, a, Np)
-    got = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a)).cpu().numpy()
+    got = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a), schedule=schedule).cpu().numpy()
+    binding.scd_check_device()
     assert _rel(got, ref) <= FP32_TOL
 
 
@@ -103,14 +105,16 @@ def test_ssca_64k_config_full(torch):
     assert _rel(got, ref) <= FP32_TOL
 
 
-def test_ssca_1m_config_sampled_channels(torch):
+@pytest.mark.parametrize("schedule", ["auto", "stages"])
+def test_ssca_1m_config_sampled_channels(torch, schedule):
     """N=2^20, Np=256, BPSK+QPSK mixture at 0 dB: every channel is computed on the GPU;
     the oracle recomputes 5 full channel rows (2^20 bins each)."""
     w = signals.ssca_mixture_1m()
     x, Np = w["x"], w["Np"]
     N = x.shape[0]
     a = orc.hamming_window(Np)
-    got_t = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a))
+    got_t = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a), schedule=schedule)
+    binding.scd_check_device()
     ch = np.array([0, 97, 128, 200, 255])
     ref = orc.ssca(x, a, Np, channels=ch, chunk=1 << 16)
     got = got_t[torch.from_numpy(ch).cuda()].cpu().numpy()

@@ -59,12 +59,14 @@ def test_fam_split_paper_scale_sampled(torch):
     assert err <= SPLIT_TOL
 
 
+@pytest.mark.parametrize("schedule", ["auto", "stages"])
 @pytest.mark.parametrize("N,Np", [(1 << 12, 16), (1 << 12, 256), (1 << 13, 32), (1 << 14, 64), (1 << 15, 128)])
-def test_ssca_split_matches_oracle(torch, N, Np):
+def test_ssca_split_matches_oracle(torch, N, Np, schedule):
     x = signals.modulated("qpsk", N, 4, 0.1, 5.0, seed=6000 + Np)
     a = orc.hamming_window(Np)
     ref = orc.ssca(x, a, Np)
-    got = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a), precision="split").cpu().numpy()
+    got = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a), precision="split",
+                           schedule=schedule).cpu().numpy()
     binding.scd_check_device()
     err = _rel(got, ref)
     print(f"SSCA split N={N} Np={Np}: max err / max|S| = {err:.3e}")
