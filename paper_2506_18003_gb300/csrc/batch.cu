@@ -178,7 +178,7 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
     constexpr int C = TileShape<MV>::C;                                                     \
     const int per = t.M2 / C;                                                               \
     const int64_t kh = tile / per;                                                          \
-    ssca_cols_tile<MV, TC>(sm, ctx, ws + (t.ch0 + kh) * t.N, A.ws + t.mid_off + kh * t.N, t.N, t.M2, t.wN, \
+    ssca_cols_tile<MV, TC, true>(sm, ctx, ws + (t.ch0 + kh) * t.N, A.ws + t.mid_off + kh * t.N, t.N, t.M2, t.wN, \
                            t.cols, t.tw, (int)(tile % per) * C);                            \
   } break;
       SCD_CO(64) SCD_CO(128) SCD_CO(256) SCD_CO(512) SCD_CO(1024)
@@ -193,7 +193,7 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
     constexpr int C = TileShape<MV>::C;                                                     \
     const int per = t.M1 / C;                                                               \
     const int64_t kh = tile / per;                                                          \
-    ssca_rows_tile<MV, TC>(sm, ctx, A.ws + t.mid_off + kh * t.N, out + (t.ch0 + kh) * t.N, t.M1, t.tw, \
+    ssca_rows_tile<MV, TC, true>(sm, ctx, A.ws + t.mid_off + kh * t.N, out + (t.ch0 + kh) * t.N, t.M1, t.tw, \
                            (int)(tile % per) * C);                                          \
   } break;
       SCD_RO(64) SCD_RO(128) SCD_RO(256) SCD_RO(512) SCD_RO(1024)

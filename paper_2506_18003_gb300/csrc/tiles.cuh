@@ -101,7 +101,9 @@ __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const floa
 // channel row `in` (N values, viewed [m1][m2], n = m1 M2 + m2), columns m20 .. m20 + C - 1:
 // M1-point DFT over m1, times the rotate factor W_N^{(m2 m1') mod N}, to `out` (may equal in)
 // at [m1'][m2].  wN = W_N^j table, cols = W_N^{c m1'} at [m1'][c].
-template <int M1, bool TC>
+// DISCARD: the input (X_g) is dead once this tile has read it and `out` is another buffer:
+// the tile's whole L2 lines of it are discarded so that they are never written back.
+template <int M1, bool TC, bool DISCARD = false>
 __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const float2* in, float2* out, int N, int M2,
                                                const float2* __restrict__ wN, const float2* __restrict__ cols,
                                                const float2* __restrict__ tw, int m20) {
@@ -117,6 +119,14 @@ __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const flo
     ob[(int64_t)f * M2] = cmul(v, w);
   };
   tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  if constexpr (DISCARD && C * 8 % 128 == 0) {                   // the tile owns whole lines of each row
+    __syncthreads();                                            // every read of the input is done
+    constexpr int LPR = C * 8 / 128;                            // lines per row
+    for (int l = threadIdx.x; l < M1 * LPR; l += blockDim.x) {
+      const char* p = reinterpret_cast<const char*>(in + (int64_t)(l / LPR) * M2 + m20) + (l % LPR) * 128;
+      asm volatile("discard.global.L2 [%0], 128;" :: "l"(p) : "memory");
+    }
+  }
 }
 
 // ---------------------------------------------------------------- SSCA row pass (K4b)
@@ -126,7 +136,10 @@ __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const flo
 template <int M2>
 __host__ __device__ constexpr int rows_stage_bytes() { return M2 * (TileShape<M2>::C + 1) * 8; }
 
-template <int M2, bool TC>
+// SLOT: the input rows are a rotating slot of the persistent schedule, dead once read: their
+// L2 lines are discarded (never written back), and the output is stored with the streaming
+// hint so that it does not push the live slots out of L2.
+template <int M2, bool TC, bool SLOT = false>
 __device__ __forceinline__ void ssca_rows_tile(float2* sm, TcCtx& ctx, const float2* in, float2* __restrict__ out,
                                                int M1, const float2* __restrict__ tw, int r0) {
   using S = TileShape<M2>;
@@ -136,10 +149,17 @@ __device__ __forceinline__ void ssca_rows_tile(float2* sm, TcCtx& ctx, const flo
   auto dst = [&](int c, int f, float2 v) { sm[f * (C + 1) + c] = v; };
   tile_fft<M2, C, false, true, S::NT, TC>(sm, tw, ctx, src, dst);
   __syncthreads();
+  if constexpr (SLOT) {                                        // C rows of M2 values, 128-byte aligned
+    const char* base = reinterpret_cast<const char*>(in + (int64_t)r0 * M2);
+    for (int l = threadIdx.x; l < C * M2 * 8 / 128; l += blockDim.x)
+      asm volatile("discard.global.L2 [%0], 128;" :: "l"(base + (int64_t)l * 128) : "memory");
+  }
   float2* __restrict__ o = out + r0;
   for (int e = threadIdx.x; e < C * M2; e += blockDim.x) {
     const int c = e % C, f = e / C;
-    o[c + (int64_t)M1 * ((f + M2 / 2) & (M2 - 1))] = sm[f * (C + 1) + c];
+    float2* dstp = o + c + (int64_t)M1 * ((f + M2 / 2) & (M2 - 1));
+    if constexpr (SLOT) __stcs(dstp, sm[f * (C + 1) + c]);
+    else *dstp = sm[f * (C + 1) + c];
   }
 }
 
