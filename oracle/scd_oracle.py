@@ -23,8 +23,13 @@ Conventions (fs = 1; all axes stored "fftshifted"):
   * windows g, g_d of the SCD low-pass (Sec. II-A, II-B, II-C) are rectangular (= 1);
   * no 1/N or 1/P scaling anywhere: raw sums.
 
-Pins (tests/test_oracle_*.py): brute-force triple sums on tiny inputs, direct vs fft
-mode, the averaged-periodogram identity at alpha = 0 (also against scipy's Welch
+Besides the auto estimate (the paper's case) both estimators take a second signal y
+(the cross estimate of Sec. II-A, Eq. II.A-SCD function) and a conjugate form (the
+product without the conjugation); alpha profiles are the column maxima of the maps.
+
+Pins (tests/test_oracle_*.py): brute-force triple sums on tiny inputs (auto, cross and
+conjugate), direct vs fft mode, cross Hermitian symmetry, the conjugate estimate as a
+cross estimate against conj(y) with the l axis reversed, the averaged-periodogram identity at alpha = 0 (also against scipy's Welch
 estimate), the lag-windowed correlogram at alpha = 0 for SSCA, exact conjugate
 symmetry (FAM), exact channel-shift invariance, |c|^2 scaling, the closed-form FAM
 response to sums of channel-centred tones, cyclic-feature locations of BPSK, and the
@@ -50,6 +55,8 @@ __all__ = [
     "ssca_map",
     "fam_map_coords",
     "ssca_map_coords",
+    "fam_alpha_profile",
+    "ssca_alpha_profile",
 ]
 
 
@@ -66,6 +73,16 @@ def twiddle(M: int, idx) -> np.ndarray:
     reduced exactly to [0, M) as an integer before it is turned into an angle."""
     j = np.mod(np.asarray(idx, dtype=np.int64), M)
     return np.exp(-2j * np.pi * (j.astype(np.float64) / M))
+
+
+def _partner(x, y):
+    """The second signal of a cross estimate (Sec. II-A, Eq. II.A-SCD function pairs the
+    demodulates of x and y); y = None is the auto estimate, y = x."""
+    if y is None:
+        return x
+    if np.asarray(y).shape != np.asarray(x).shape:
+        raise ValueError("x and y must have the same length")
+    return y
 
 
 def _promote(x, a):
@@ -119,28 +136,37 @@ def _fam_second_fft(z: np.ndarray, P: int, mode: str) -> np.ndarray:
     return _dft_rows(z, P, q, mode)
 
 
-def fam_pairs(x, a, Np: int, L: int, P: int, kh, lh, mode: str = "fft") -> np.ndarray:
+def fam_pairs(x, a, Np: int, L: int, P: int, kh, lh, mode: str = "fft", y=None,
+              conjugate: bool = False) -> np.ndarray:
     """FAM estimate for selected channel pairs (kh[i], lh[i]) (Sec. II-B-2,
     Eq. II.B-SCD_function_FAM with g_d = 1):
 
-        S(k, l, q) = sum_{p<P} X(p, k) conj(X(p, l)) W_P^{(q p) mod P}
+        S(k, l, q) = sum_{p<P} X(p, k) conj(Y(p, l)) W_P^{(q p) mod P}
 
-    i.e. the conjugate multiplication followed by the P-point FFT.  Returns complex128
-    [len(kh)][P (qh)].
+    i.e. the conjugate multiplication followed by the P-point FFT.  Y is the channeliser
+    output of y (Eq. II.A-SCD function's cross form; y = None: Y = X, the auto estimate).
+    conjugate=True forms the conjugate estimate: the product X(p, k) Y(p, l) without the
+    conjugation, which correlates x near f_k with y near f_l in the conjugate sense
+    (alpha = f_k + f_l + q/(P L), f = (f_k - f_l)/2).  Returns complex128 [len(kh)][P (qh)].
     """
     X = fam_demodulates(x, a, Np, L, P, mode)
+    Y = X if y is None else fam_demodulates(_partner(x, y), a, Np, L, P, mode)
     kh = np.asarray(kh, dtype=np.int64)
     lh = np.asarray(lh, dtype=np.int64)
-    z = X[kh, :] * np.conj(X[lh, :])                               # [pairs][P]
+    second = Y[lh, :] if conjugate else np.conj(Y[lh, :])
+    z = X[kh, :] * second                                          # [pairs][P]
     return _fam_second_fft(z, P, mode)
 
 
-def fam(x, a, Np: int, L: int, P: int, mode: str = "fft") -> np.ndarray:
-    """Full FAM estimate, complex128 [Np (kh)][Np (lh)][P (qh)]."""
+def fam(x, a, Np: int, L: int, P: int, mode: str = "fft", y=None, conjugate: bool = False) -> np.ndarray:
+    """Full FAM estimate, complex128 [Np (kh)][Np (lh)][P (qh)] (y, conjugate: as in
+    fam_pairs)."""
     X = fam_demodulates(x, a, Np, L, P, mode)
+    Y = X if y is None else fam_demodulates(_partner(x, y), a, Np, L, P, mode)
+    second = Y if conjugate else np.conj(Y)
     out = np.empty((Np, Np, P), dtype=np.complex128)
     for kh in range(Np):                                          # one channel row at a time
-        z = X[kh][None, :] * np.conj(X)                           # [lh][p]
+        z = X[kh][None, :] * second                               # [lh][p]
         out[kh] = _fam_second_fft(z, P, mode)
     return out
 
@@ -170,13 +196,17 @@ def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.n
     return spectra * down
 
 
-def ssca_cdp(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.ndarray:
+def ssca_cdp(x, a, Np: int, n, channels=None, mode: str = "fft", y=None,
+             conjugate: bool = False) -> np.ndarray:
     """Channel-data product of Sec. II-C, Eq. Xg with g = 1:
-    X_g(n, k) = X_T(n, k) conj(x[n]).  Returns complex128 [len(channels)][len(n)]."""
+    X_g(n, k) = X_T(n, k) conj(y[n]), y = x for the auto estimate (Sec. II-C multiplies
+    the demodulate by the conjugated second signal).  conjugate=True multiplies by y[n]
+    itself (the conjugate estimate).  Returns complex128 [len(channels)][len(n)]."""
     n = np.asarray(n, dtype=np.int64)
     XT = ssca_demodulates(x, a, Np, n, channels, mode)            # [n][ch]
-    conj_x = np.conj(np.asarray(x).astype(np.complex128)[n])
-    return (XT * conj_x[:, None]).T
+    yn = np.asarray(_partner(x, y)).astype(np.complex128)[n]
+    second = yn if conjugate else np.conj(yn)
+    return (XT * second[:, None]).T
 
 
 def ssca_strip(Xg_row: np.ndarray, mode: str = "fft") -> np.ndarray:
@@ -191,14 +221,17 @@ def ssca_strip(Xg_row: np.ndarray, mode: str = "fft") -> np.ndarray:
     return np.fft.fft(Xg_row, axis=-1)[..., np.mod(q, N)]
 
 
-def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13) -> np.ndarray:
+def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13, y=None,
+         conjugate: bool = False) -> np.ndarray:
     """SSCA estimate (Sec. II-C, Eq. Xg and Eq. II.B-SSCA_auto, with g = 1 and the
     time origin at the first sample):
 
-        X_g(n, k) = X_T(n, k) conj(x[n])
+        X_g(n, k) = X_T(n, k) conj(y[n])          (y = x: the auto estimate)
         S(k, q)   = sum_{n<N} X_g(n, k) W_N^{(q n) mod N},   q in [-N/2, N/2)
 
-    alpha = k/Np + q/N and f = (k/Np - q/N)/2.  Returns complex128
+    alpha = k/Np + q/N and f = (k/Np - q/N)/2.  conjugate=True uses y[n] unconjugated;
+    the bin then correlates x at f_k with y at q/N in the conjugate sense, whose
+    alpha = f_k + q/N and f = (f_k - q/N)/2 are the same coordinates.  Returns complex128
     [len(channels)][N (sh)], sh = q + N/2.
     """
     N = np.asarray(x).shape[0]
@@ -206,7 +239,7 @@ def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13) 
     Xg = np.empty((kh.shape[0], N), dtype=np.complex128)          # channel-major CDP
     for n0 in range(0, N, chunk):                                 # channeliser in chunks of time
         n = np.arange(n0, min(N, n0 + chunk), dtype=np.int64)
-        Xg[:, n0:n0 + n.shape[0]] = ssca_cdp(x, a, Np, n, kh, mode)
+        Xg[:, n0:n0 + n.shape[0]] = ssca_cdp(x, a, Np, n, kh, mode, y, conjugate)
     if mode == "direct":
         return ssca_strip(Xg, mode)                               # one DFT-matrix product
     out = np.empty_like(Xg)
@@ -216,7 +249,7 @@ def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13) 
 
 
 # ----------------------------------------------------------------------------- maps
-def fam_map_coords(Np: int, L: int, P: int):
+def fam_map_coords(Np: int, L: int, P: int, conjugate: bool = False):
     """Kept FAM cells and their (f, alpha) grid positions.
 
     Algorithm 1 (`FFT2`) keeps only the central half of each P-point output.  Here the
@@ -224,6 +257,9 @@ def fam_map_coords(Np: int, L: int, P: int):
     f = (f_k + f_l)/2 and alpha = f_k - f_l + q/(P L) (Sec. II-B-2), so with integer
     grid indices fh = k + l + Np (f = (fh - Np)/(2 Np)) and
     ah = (k - l) Q + q + P L (alpha = (ah - P L)/(P L)).
+    The conjugate estimate has f = (f_k - f_l)/2 and alpha = f_k + f_l + q/(P L):
+    fh = k - l + Np, ah = (k + l) Q + q + P L; the cells with alpha < -1 (ah < 0, only
+    at k = l = -Np/2) fall outside the principal domain and are not kept.
     Returns int64 arrays kh, lh, qh, fh, ah (one entry per kept cell).
     """
     if (P * L) % Np or 2 * L > Np:
@@ -232,13 +268,17 @@ def fam_map_coords(Np: int, L: int, P: int):
     k = _signed_channels(Np)
     kk, ll, qq = np.meshgrid(k, k, np.arange(-Q, Q, dtype=np.int64), indexing="ij")
     kk, ll, qq = kk.ravel(), ll.ravel(), qq.ravel()
-    return (kk + Np // 2, ll + Np // 2, qq + P // 2, kk + ll + Np, (kk - ll) * Q + qq + P * L)
+    if not conjugate:
+        return (kk + Np // 2, ll + Np // 2, qq + P // 2, kk + ll + Np, (kk - ll) * Q + qq + P * L)
+    ah = (kk + ll) * Q + qq + P * L
+    keep = ah >= 0
+    return (kk[keep] + Np // 2, ll[keep] + Np // 2, qq[keep] + P // 2, (kk - ll + Np)[keep], ah[keep])
 
 
-def fam_map(S: np.ndarray, Np: int, L: int, P: int, power: int = 1) -> np.ndarray:
+def fam_map(S: np.ndarray, Np: int, L: int, P: int, power: int = 1, conjugate: bool = False) -> np.ndarray:
     """Scatter |S|^power of the kept FAM cells onto the float64 [2 Np][2 P L] grid;
     cells that no (k, l, q) reaches stay 0."""
-    kh, lh, qh, fh, ah = fam_map_coords(Np, L, P)
+    kh, lh, qh, fh, ah = fam_map_coords(Np, L, P, conjugate)
     grid = np.zeros((2 * Np, 2 * P * L), dtype=np.float64)
     grid[fh, ah] = np.abs(S[kh, lh, qh]) ** power
     return grid
@@ -269,3 +309,18 @@ def ssca_map(S: np.ndarray, N: int, Np: int, power: int = 1) -> np.ndarray:
     grid = np.zeros((Np, 2 * N), dtype=np.float64)
     grid[fh, ah] = np.abs(S[kh, sh]) ** power
     return grid
+
+
+# ----------------------------------------------------------------------------- alpha profiles
+def fam_alpha_profile(S: np.ndarray, Np: int, L: int, P: int, power: int = 1,
+                      conjugate: bool = False) -> np.ndarray:
+    """Cycle-frequency profile: for every alpha column ah of the FAM map, the largest
+    |S|^power over f (the feature vector the paper's RFML motivation, Sec. I, extracts
+    from the SCD).  Columns that no cell reaches are 0.  Returns float64 [2 P L]."""
+    return fam_map(S, Np, L, P, power, conjugate).max(axis=0)
+
+
+def ssca_alpha_profile(S: np.ndarray, N: int, Np: int, power: int = 1) -> np.ndarray:
+    """Cycle-frequency profile of the SSCA map: largest |S|^power over f per alpha column
+    ah.  Returns float64 [2 N]."""
+    return ssca_map(S, N, Np, power).max(axis=0)
