@@ -469,6 +469,68 @@ def run_reference(args):
     return 0
 
 
+def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
+    """Times the cross / conjugate estimates and the alpha profiles at the paper-scale sizes
+    (FAM N=65,728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256), outside the step's timed region:
+    CUDA events on the launching stream around `reps` calls after `warmup` calls; HBM
+    fraction on algorithmic bytes (inputs read + outputs written)."""
+    from paper_2506_18003_gb300 import signals
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, ValueError, KeyError):
+        hbm = 6800.0
+    wf = signals.fam_qam16_paper_scale()
+    ws_ = signals.ssca_mixture_1m()
+    Np, L, P, Nf = 256, 64, 1024, wf["x"].shape[0]
+    Ns, Nps = ws_["x"].shape[0], 256
+    Q = P * L // Np
+    xf = torch.from_numpy(wf["x"]).to(dev)
+    yf = torch.from_numpy(signals.modulated("qpsk", Nf, 4, 0.1, 10.0, seed=5100)).to(dev)
+    xs = torch.from_numpy(ws_["x"]).to(dev)
+    ys = torch.from_numpy(signals.modulated("qpsk", Ns, 4, 0.05, 5.0, seed=6200)).to(dev)
+    Sf = torch.empty((Np, Np, P), dtype=torch.complex64, device=dev)
+    Ss = torch.empty((Nps, Ns), dtype=torch.complex64, device=dev)
+    pf = torch.empty(2 * P * L, dtype=torch.float32, device=dev)
+    ps = torch.empty(2 * Ns, dtype=torch.float32, device=dev)
+    lib = binding.load()
+    work = torch.empty(max(lib.scd_fam_workspace_bytes(Nf, Np, L, P, 0), lib.scd_ssca_workspace_bytes(Ns, Nps, 0)),
+                       dtype=torch.uint8, device=dev)
+    used = (P - 1) * L + Np
+    cases = {
+        "fam_cross": (lambda: binding.scd_fam(xf, Np, L, P, out=Sf, stream=stream, workspace=work, y=yf),
+                      16 * used + 8 * Np * Np * P),
+        "fam_conjugate": (lambda: binding.scd_fam(xf, Np, L, P, out=Sf, stream=stream, workspace=work, conjugate=True),
+                          8 * used + 8 * Np * Np * P),
+        "fam_alpha_profile": (lambda: binding.scd_fam_alpha_profile(Sf, Np, L, P, pf, stream=stream),
+                              8 * Np * Np * 2 * Q + 4 * 2 * P * L),
+        "ssca_cross": (lambda: binding.scd_ssca(xs, Nps, out=Ss, stream=stream, workspace=work, y=ys),
+                       16 * Ns + 8 * Nps * Ns),
+        "ssca_conjugate": (lambda: binding.scd_ssca(xs, Nps, out=Ss, stream=stream, workspace=work, conjugate=True),
+                           8 * Ns + 8 * Nps * Ns),
+        "ssca_alpha_profile": (lambda: binding.scd_ssca_alpha_profile(Ss, Ns, Nps, ps, stream=stream),
+                               8 * Nps * Ns + 4 * 2 * Ns),
+    }
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, (fn, nbytes) in cases.items():
+            for _ in range(warmup):
+                fn()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                fn()
+            t1.record(stream)
+            t1.synchronize()
+            ms = t0.elapsed_time(t1) / reps
+            out[name] = {"ms": round(ms, 5), "algorithmic_bytes": nbytes,
+                         "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4)}
+    binding.scd_check_device(stream)
+    del Sf, Ss, work
+    torch.cuda.empty_cache()
+    out["sizes"] = "FAM N=65728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256; FP32 form; %d calls each" % reps
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -563,6 +625,8 @@ def run_ours(args):
     if not args.no_e2e:
         with torch.cuda.stream(stream):
             line["e2e"] = wl.e2e(prec, stream, min(args.steps, args.e2e_steps), world, torch)
+    if not args.no_variants:
+        line["variants"] = measure_variants(torch, binding, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, desc = wl.oracle_sample()
         line["cpu_baseline"] = {"value": wl.samples_per_step() / t / 1e6, "unit": "Msamples/s", "cores": 1,
@@ -587,6 +651,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default sizing)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the cross / conjugate / alpha-profile timings at paper-scale sizes")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -64,7 +64,7 @@ typedef enum { SCD_FP32 = 0, SCD_SPLIT_BF16 = 1 } scd_precision;
 typedef enum { SCD_SCHEDULE_AUTO = 0, SCD_SCHEDULE_STAGES = 1, SCD_SCHEDULE_PERSISTENT = 2 } scd_schedule;
 
 /* Options.  Pass NULL for defaults: legacy default stream, FP32, no workspace, |S|,
- * no stage events.  Zero-initialise the struct before filling it. */
+ * no stage events, auto estimate.  Zero-initialise the struct before filling it. */
 typedef struct {
   void* stream;             /* cudaStream_t to enqueue on */
   int32_t precision;        /* scd_precision */
@@ -75,11 +75,22 @@ typedef struct {
    * least (kernels launched by the call) + 1, event i (a cudaEvent_t, see
    * scd_events_create) is recorded on the stream just before the call's i-th kernel and
    * the next one after its last kernel.  scd_fam launches 2 kernels (channeliser, pair
-   * FFT); scd_ssca 3 with the STAGES schedule (channeliser + CDP, column pass, row pass) or 1
-   * with PERSISTENT (AUTO resolves to one of the two); each map 1. */
+   * FFT; 3 for a cross or conjugate estimate: channeliser of x, of y, pair FFT); scd_ssca 3
+   * with the STAGES schedule (channeliser + CDP, column pass, row pass) or 1 with PERSISTENT
+   * (AUTO resolves to one of the two); each map and profile 1. */
   void** stage_events;
   int32_t n_stage_events;
   int32_t schedule;         /* scd_ssca only: scd_schedule */
+  /* Second signal of a cross estimate (Sec. II-A, Eq. II.A-SCD function correlates the
+   * demodulates of x and y): complex64[N] device pointer, the same length as x, used by
+   * scd_fam and scd_ssca in place of x wherever the estimate conjugates (FAM: the second
+   * channeliser output; SSCA: the factor y[n] of the channel-data product, as Sec. II-C
+   * describes).  NULL = the auto estimate (y = x).  Host-buffer variants: must be NULL. */
+  const void* y;
+  /* 1 = conjugate estimate: the second factor is not conjugated (FAM: X(p,k) Y(p,l); SSCA:
+   * X_T(n,k) y[n]); it correlates x near f1 with y near f2 at alpha = f1 + f2.  Used by
+   * scd_fam, scd_ssca, scd_fam_map and scd_fam_alpha_profile; 0 = the paper's estimate. */
+  int32_t conjugate;
 } scd_opts;
 
 /* ------------------------------------------------------------------------------ FAM
@@ -88,13 +99,16 @@ typedef struct {
  *   X(p,k)   = W_Np^{(k p L) mod Np} * sum_{n<Np} a[n] x[pL+n] W_Np^{(k n) mod Np}
  *   S(k,l,q) = sum_{p<P} X(p,k) conj(X(p,l)) W_P^{(q p) mod P}
  * alpha = (k - l)/Np + q/(P L), f = (k + l)/(2 Np).
+ * Cross estimate (opts->y): X(p,l) in the product is replaced by the same demodulate of y.
+ * Conjugate estimate (opts->conjugate): S(k,l,q) = sum_p X(p,k) Y(p,l) W_P^{(q p) mod P}
+ * with Y = X or y's demodulate; alpha = (k + l)/Np + q/(P L), f = (k - l)/(2 Np).
  *   x       complex64[N], N >= (P-1) L + Np (later samples are ignored)
  *   Np      channels, power of two in [16, 256] (the paper's range 2^4..2^8)
  *   L       hop between blocks, 1 <= L
  *   P       blocks, power of two in [2, 16384]
  *   window  float32[Np] or NULL (Hamming)
  *   out     complex64[Np][Np][P], out[kh][lh][qh] = S(k, l, q)
- *   opts    workspace >= scd_fam_workspace_bytes(...) bytes
+ *   opts    workspace >= scd_fam_workspace_bytes(...) bytes (covers every variant)
  * Errors: SCD_ERR_ARG (NULL/misaligned pointers, N too short, L < 1),
  *         SCD_ERR_UNSUPPORTED (Np or P out of range / not a power of two, precision),
  *         SCD_ERR_WORKSPACE, SCD_ERR_CUDA. */
@@ -109,7 +123,9 @@ SCD_API size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t
  *   X_T(n,k) = W_Np^{(k s) mod Np} sum_{r<Np} a[r] x[s+r] W_Np^{(k r) mod Np},  s = n - Np/2
  *   X_g(n,k) = X_T(n,k) conj(x[n])
  *   S(k,q)   = sum_{n<N} X_g(n,k) W_N^{(q n) mod N}
- * alpha = k/Np + q/N, f = (k/Np - q/N)/2.  The N-point transform is the decomposed
+ * alpha = k/Np + q/N, f = (k/Np - q/N)/2.  Cross estimate (opts->y): conj(y[n]) replaces
+ * conj(x[n]); conjugate estimate (opts->conjugate): y[n] (or x[n]) unconjugated, with the
+ * same alpha and f (x near f_k paired with y near q/N: alpha = f_k + q/N).  The N-point transform is the decomposed
  * (four-step) FFT of Sec. III-B-1 (Eq. Chap4_2DFFT) with N = M1 M2.
  *   x       complex64[N], N a power of two in [2^12, 2^20] (Sec. III-B-2's range)
  *   Np      power of two in [16, 256]
@@ -128,6 +144,8 @@ SCD_API size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision
  *   fh = k + l + Np            (f = (fh - Np)/(2 Np))
  *   ah = (k - l) Q + q + P L   (alpha = (ah - P L)/(P L))
  * No two cells share a grid point; grid points no cell reaches are written as 0.
+ * With opts->conjugate (the output of a conjugate scd_fam): fh = k - l + Np,
+ * ah = (k + l) Q + q + P L; the cells with alpha < -1 (k = l = -Np/2, q < 0) are not kept.
  *   S    complex64[Np][Np][P] (scd_fam's output)
  *   map  float32[2 Np][2 P L], 16-byte aligned, fully overwritten
  * Needs P L divisible by Np and 2 L <= Np (else SCD_ERR_UNSUPPORTED). */
@@ -140,6 +158,19 @@ SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, 
  *   S    complex64[Np][N] (scd_ssca's output)
  *   map  float32[Np][2 N], 16-byte aligned, fully overwritten (unreached points are 0) */
 SCD_API scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts);
+
+/* ------------------------------------------------------------------------------ alpha profiles
+ * Cycle-frequency profile: for every alpha column ah of the map above, the largest
+ * |S|^map_power over f (0 where no cell lands), the feature vector that the paper's RFML
+ * motivation (Sec. I) draws from the SCD.  Computed straight from S (the map itself is not
+ * formed); deterministic (a max, no atomics).
+ *   scd_fam_alpha_profile   S complex64[Np][Np][P]; profile float32[2 P L]; limits and
+ *                           opts->conjugate as scd_fam_map
+ *   scd_ssca_alpha_profile  S complex64[Np][N]; profile float32[2 N]
+ * profile is a device pointer, 16-byte aligned, fully overwritten. */
+SCD_API scd_status scd_fam_alpha_profile(const void* S, int32_t Np, int32_t L, int32_t P, float* profile,
+                                         const scd_opts* opts);
+SCD_API scd_status scd_ssca_alpha_profile(const void* S, int64_t N, int32_t Np, float* profile, const scd_opts* opts);
 
 /* ------------------------------------------------------------------------------ batches
  * Batched form: nsig signals of uneven lengths through ONE persistent kernel launch (a
@@ -220,7 +251,8 @@ SCD_API size_t scd_ssca_host_workspace_bytes(int64_t N, int32_t Np, int32_t prec
  * the library until the process exits), and calls no cudaMalloc, cudaFree or allocating
  * library routine.  Arguments, output and results are those of scd_fam (opts->workspace is
  * ignored), with one more limit: Np * P <= 262144 (e.g. Np = 256 with P <= 1024);
- * larger sizes return SCD_ERR_UNSUPPORTED and scd_last_error() names the limit.
+ * larger sizes return SCD_ERR_UNSUPPORTED and scd_last_error() names the limit.  Only the
+ * auto estimate: opts->y or opts->conjugate set gives SCD_ERR_UNSUPPORTED.
  * All calls share the scratch array, which keeps the last call's contents (each call
  * rewrites everything it reads, so nothing has to start at zero); calls whose executions
  * overlap on the same GPU race on it and must be serialised by the caller.  The first call

@@ -28,6 +28,8 @@ class ScdOpts(ctypes.Structure):
         ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
         ("n_stage_events", ctypes.c_int32),
         ("schedule", ctypes.c_int32),
+        ("y", ctypes.c_void_p),
+        ("conjugate", ctypes.c_int32),
     ]
 
 
@@ -42,6 +44,8 @@ SIGNATURES = {
     "scd_ssca_workspace_bytes": (_sz, [_i64, _i32, _i32]),
     "scd_fam_map": (_i32, [_vp, _i32, _i32, _i32, _vp, _opts_p]),
     "scd_ssca_map": (_i32, [_vp, _i64, _i32, _vp, _opts_p]),
+    "scd_fam_alpha_profile": (_i32, [_vp, _i32, _i32, _i32, _vp, _opts_p]),
+    "scd_ssca_alpha_profile": (_i32, [_vp, _i64, _i32, _vp, _opts_p]),
     "scd_fam_host": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp, _opts_p]),
     "scd_fam_host_workspace_bytes": (_sz, [_i64, _i32, _i32, _i32, _i32]),
     "scd_ssca_host": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p]),
@@ -132,10 +136,13 @@ def _need(t, dtype, numel, name):
 SCHEDULES = {"auto": 0, "stages": 1, "persistent": 2}
 
 
-def make_opts(stream=None, precision="fp32", workspace=None, map_power=1, schedule="auto") -> ScdOpts:
+def make_opts(stream=None, precision="fp32", workspace=None, map_power=1, schedule="auto", y=None,
+              conjugate=False) -> ScdOpts:
     o = ScdOpts()
     o.stream = _stream(stream)
     o.schedule = SCHEDULES[schedule]
+    o.y = None if y is None else y.data_ptr()
+    o.conjugate = 1 if conjugate else 0
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.map_power = int(map_power)
     if workspace is not None:
@@ -151,12 +158,24 @@ def _workspace(nbytes, device, workspace):
     return torch.empty(max(1, nbytes), dtype=torch.uint8, device=device)
 
 
-def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32", stream=None, workspace=None):
-    """FAM estimate of the complex64 CUDA tensor x; returns complex64 [Np, Np, P]."""
+def _partner(x, y):
+    torch = _torch()
+    if y is not None:
+        _need(y, torch.complex64, x.numel(), "y")
+        if y.numel() != x.numel():
+            raise TypeError("y must have as many samples as x")
+    return y
+
+
+def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32", stream=None, workspace=None,
+            y=None, conjugate=False):
+    """FAM estimate of the complex64 CUDA tensor x; returns complex64 [Np, Np, P].
+    y: second signal of a cross estimate; conjugate: the conjugate estimate."""
     torch = _torch()
     lib = load()
     _need(x, torch.complex64, 1, "x")
     N = x.numel()
+    y = _partner(x, y)
     if window is not None:
         _need(window, torch.float32, Np, "window")
     if out is None:
@@ -164,17 +183,20 @@ def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32",
     _need(out, torch.complex64, Np * Np * P, "out")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     ws = _workspace(lib.scd_fam_workspace_bytes(N, Np, L, P, prec), x.device, workspace)
-    o = make_opts(stream, prec, ws)
+    o = make_opts(stream, prec, ws, y=y, conjugate=conjugate)
     check(lib.scd_fam(_ptr(x), N, Np, L, P, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_fam")
     return out
 
 
-def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None, schedule="auto"):
-    """SSCA estimate of the complex64 CUDA tensor x (N = x.numel()); returns complex64 [Np, N]."""
+def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None, schedule="auto",
+             y=None, conjugate=False):
+    """SSCA estimate of the complex64 CUDA tensor x (N = x.numel()); returns complex64 [Np, N].
+    y: second signal of a cross estimate; conjugate: the conjugate estimate."""
     torch = _torch()
     lib = load()
     _need(x, torch.complex64, 1, "x")
     N = x.numel()
+    y = _partner(x, y)
     if window is not None:
         _need(window, torch.float32, Np, "window")
     if out is None:
@@ -182,20 +204,21 @@ def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, w
     _need(out, torch.complex64, Np * N, "out")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     ws = _workspace(lib.scd_ssca_workspace_bytes(N, Np, prec), x.device, workspace)
-    o = make_opts(stream, prec, ws, schedule=schedule)
+    o = make_opts(stream, prec, ws, schedule=schedule, y=y, conjugate=conjugate)
     check(lib.scd_ssca(_ptr(x), N, Np, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_ssca")
     return out
 
 
-def scd_fam_map(S, Np: int, L: int, P: int, map=None, power: int = 1, stream=None):
-    """(f, alpha) grid float32 [2 Np, 2 P L] of a FAM estimate S."""
+def scd_fam_map(S, Np: int, L: int, P: int, map=None, power: int = 1, stream=None, conjugate=False):
+    """(f, alpha) grid float32 [2 Np, 2 P L] of a FAM estimate S (conjugate: of a conjugate
+    estimate)."""
     torch = _torch()
     lib = load()
     _need(S, torch.complex64, Np * Np * P, "S")
     if map is None:
         map = torch.empty((2 * Np, 2 * P * L), dtype=torch.float32, device=S.device)
     _need(map, torch.float32, 4 * Np * P * L, "map")
-    o = make_opts(stream, "fp32", None, power)
+    o = make_opts(stream, "fp32", None, power, conjugate=conjugate)
     check(lib.scd_fam_map(_ptr(S), Np, L, P, _ptr(map), ctypes.byref(o)), "scd_fam_map")
     return map
 
@@ -211,6 +234,32 @@ def scd_ssca_map(S, N: int, Np: int, map=None, power: int = 1, stream=None):
     o = make_opts(stream, "fp32", None, power)
     check(lib.scd_ssca_map(_ptr(S), N, Np, _ptr(map), ctypes.byref(o)), "scd_ssca_map")
     return map
+
+
+def scd_fam_alpha_profile(S, Np: int, L: int, P: int, profile=None, power: int = 1, stream=None, conjugate=False):
+    """Largest |S|^power over f per alpha column of the FAM map: float32 [2 P L]."""
+    torch = _torch()
+    lib = load()
+    _need(S, torch.complex64, Np * Np * P, "S")
+    if profile is None:
+        profile = torch.empty(2 * P * L, dtype=torch.float32, device=S.device)
+    _need(profile, torch.float32, 2 * P * L, "profile")
+    o = make_opts(stream, "fp32", None, power, conjugate=conjugate)
+    check(lib.scd_fam_alpha_profile(_ptr(S), Np, L, P, _ptr(profile), ctypes.byref(o)), "scd_fam_alpha_profile")
+    return profile
+
+
+def scd_ssca_alpha_profile(S, N: int, Np: int, profile=None, power: int = 1, stream=None):
+    """Largest |S|^power over f per alpha column of the SSCA map: float32 [2 N]."""
+    torch = _torch()
+    lib = load()
+    _need(S, torch.complex64, Np * N, "S")
+    if profile is None:
+        profile = torch.empty(2 * N, dtype=torch.float32, device=S.device)
+    _need(profile, torch.float32, 2 * N, "profile")
+    o = make_opts(stream, "fp32", None, power)
+    check(lib.scd_ssca_alpha_profile(_ptr(S), N, Np, _ptr(profile), ctypes.byref(o)), "scd_ssca_alpha_profile")
+    return profile
 
 
 def scd_ssca_tune(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None, reps=3):

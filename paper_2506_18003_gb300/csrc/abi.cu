@@ -24,7 +24,7 @@ scd_status cuda_fail(cudaError_t e) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-const scd_opts kDefaultOpts = {nullptr, SCD_FP32, 1, nullptr, 0, nullptr, 0, SCD_SCHEDULE_AUTO};
+const scd_opts kDefaultOpts = {nullptr, SCD_FP32, 1, nullptr, 0, nullptr, 0, SCD_SCHEDULE_AUTO, nullptr, 0};
 
 // Records opts.stage_events[i] (when the caller asked for at least `needed` events).
 struct StageMarks {
@@ -63,6 +63,11 @@ scd_status check_ssca(const void* x, int64_t N, int32_t Np, const float* window,
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// The variant fields: y (when given) a complex64 device array aligned like x; conjugate 0 / 1.
+bool variant_ok(const scd_opts& o) {
+  return (!o.y || aligned(o.y, 8)) && (o.conjugate == 0 || o.conjugate == 1);
+}
+
 }  // namespace
 
 namespace scd {
@@ -74,7 +79,7 @@ extern "C" {
 size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t P, int32_t precision) {
   (void)N; (void)L; (void)precision;
   if (Np < 1 || P < 1) return 0;
-  return round_up(sizeof(float) * 2 * (size_t)Np * (size_t)P, 256);   // X[kh][p]
+  return 2 * round_up(sizeof(float) * 2 * (size_t)Np * (size_t)P, 256);   // X[kh][p], Y[lh][p]
 }
 
 size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision) {
@@ -90,6 +95,7 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
   if (s != SCD_OK) return s;
   const scd_opts& o = opts_or_default(opts);
   if (o.precision != SCD_FP32 && o.precision != SCD_SPLIT_BF16) return SCD_ERR_UNSUPPORTED;
+  if (!variant_ok(o)) return SCD_ERR_ARG;
   const size_t need = scd_fam_workspace_bytes(N, Np, L, P, o.precision);
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
@@ -100,12 +106,25 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
     if (!window) return cuda_fail(e);
   }
   float2* X = (float2*)o.workspace;
-  StageMarks m{o, 3};
-  if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
+  const bool partner = o.y || o.conjugate;
+  StageMarks m{o, partner ? 4 : 3};
+  int mk = 0;
+  if ((e = m.mark(mk++, st)) != cudaSuccess) return cuda_fail(e);
   if ((e = scd::fam_channelise((const float2*)x, Np, L, P, window, X, st, o.precision)) != cudaSuccess) return cuda_fail(e);
-  if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::fam_pair_fft(X, Np, P, (float2*)out, st, o.precision)) != cudaSuccess) return cuda_fail(e);
-  if ((e = m.mark(2, st)) != cudaSuccess) return cuda_fail(e);
+  const float2* Y = X;
+  if (partner) {
+    // the second operand: y's (or x's) demodulates, conjugated for the conjugate estimate so
+    // that the pair kernel's X conj(Y) becomes X Y
+    float2* Z = (float2*)((char*)o.workspace + scd_fam_workspace_bytes(N, Np, L, P, o.precision) / 2);
+    if ((e = m.mark(mk++, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = scd::fam_channelise((const float2*)(o.y ? o.y : x), Np, L, P, window, Z, st, o.precision,
+                                 o.conjugate != 0)) != cudaSuccess)
+      return cuda_fail(e);
+    Y = Z;
+  }
+  if ((e = m.mark(mk++, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::fam_pair_fft(X, Y, Np, P, (float2*)out, st, o.precision)) != cudaSuccess) return cuda_fail(e);
+  if ((e = m.mark(mk++, st)) != cudaSuccess) return cuda_fail(e);
   return SCD_OK;
 }
 
@@ -114,6 +133,9 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   if (s != SCD_OK) return s;
   const scd_opts& o = opts_or_default(opts);
   if (o.precision != SCD_FP32 && o.precision != SCD_SPLIT_BF16) return SCD_ERR_UNSUPPORTED;
+  if (!variant_ok(o)) return SCD_ERR_ARG;
+  const float2* y = (const float2*)(o.y ? o.y : x);
+  const bool conj = o.conjugate != 0;
   const size_t need = scd_ssca_workspace_bytes(N, Np, o.precision);
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
@@ -131,10 +153,10 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
     StageMarks m{o, 2};
     if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
     scd_status r = choice.item_bytes
-                       ? scd::ssca_persistent_tuned((const float2*)x, N, Np, window, (float2*)out, o.workspace,
+                       ? scd::ssca_persistent_tuned((const float2*)x, y, conj, N, Np, window, (float2*)out, o.workspace,
                                                     o.workspace_bytes, st, o.precision, choice.item_bytes,
                                                     choice.slot_bytes)
-                       : scd::ssca_persistent((const float2*)x, N, Np, window, (float2*)out, o.workspace,
+                       : scd::ssca_persistent((const float2*)x, y, conj, N, Np, window, (float2*)out, o.workspace,
                                               o.workspace_bytes, st, o.precision);
     if (r != SCD_OK) return r;
     if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
@@ -142,7 +164,8 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   }
   StageMarks m{o, 4};
   if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::ssca_cdp((const float2*)x, N, Np, window, ws, st, o.precision)) != cudaSuccess) return cuda_fail(e);
+  if ((e = scd::ssca_cdp((const float2*)x, y, conj, N, Np, window, ws, st, o.precision)) != cudaSuccess)
+    return cuda_fail(e);
   if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
   if ((e = scd::ssca_cols(ws, N, Np, st, o.precision)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(2, st)) != cudaSuccess) return cuda_fail(e);
@@ -151,34 +174,73 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   return SCD_OK;
 }
 
-scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts) {
-  if (!S || !map || !aligned(S, 16) || !aligned(map, 16)) return SCD_ERR_ARG;
+}  // extern "C"
+
+namespace {
+scd_status check_fam_grid(const void* S, int32_t Np, int32_t L, int32_t P, const float* dst) {
+  if (!S || !dst || !aligned(S, 16) || !aligned(dst, 16)) return SCD_ERR_ARG;
   if (L < 1) return SCD_ERR_ARG;
   if (!np_ok(Np) || P < 2 || P > 16384 || !scd::is_pow2(P)) return SCD_ERR_UNSUPPORTED;
   if (((int64_t)P * L) % Np != 0 || 2 * (int64_t)L > Np) return SCD_ERR_UNSUPPORTED;
-  const scd_opts& o = opts_or_default(opts);
-  if (o.map_power != 1 && o.map_power != 2) return SCD_ERR_ARG;
-  StageMarks m{o, 2};
-  cudaStream_t st = (cudaStream_t)o.stream;
-  cudaError_t e;
-  if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::fam_map((const float2*)S, Np, L, P, o.map_power, map, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
+  if (4 * (int64_t)Np * P * L >= (int64_t(1) << 31)) return SCD_ERR_UNSUPPORTED;
   return SCD_OK;
 }
 
-scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts) {
-  if (!S || !map || !aligned(S, 16) || !aligned(map, 16)) return SCD_ERR_ARG;
+scd_status check_ssca_grid(const void* S, int64_t N, int32_t Np, const float* dst) {
+  if (!S || !dst || !aligned(S, 16) || !aligned(dst, 16)) return SCD_ERR_ARG;
   if (!np_ok(Np) || N < 4096 || N > (1 << 20) || !scd::is_pow2(N)) return SCD_ERR_UNSUPPORTED;
-  const scd_opts& o = opts_or_default(opts);
+  return SCD_OK;
+}
+
+// Runs one map / profile kernel between stage marks 0 and 1.
+template <class Launch>
+scd_status run_one(const scd_opts& o, Launch launch) {
   if (o.map_power != 1 && o.map_power != 2) return SCD_ERR_ARG;
   StageMarks m{o, 2};
   cudaStream_t st = (cudaStream_t)o.stream;
   cudaError_t e;
   if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::ssca_map((const float2*)S, N, Np, o.map_power, map, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch(st)) != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
   return SCD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts) {
+  scd_status s = check_fam_grid(S, Np, L, P, map);
+  if (s != SCD_OK) return s;
+  const scd_opts& o = opts_or_default(opts);
+  return run_one(o, [&](cudaStream_t st) {
+    return scd::fam_map((const float2*)S, Np, L, P, o.map_power, o.conjugate != 0, map, st);
+  });
+}
+
+scd_status scd_fam_alpha_profile(const void* S, int32_t Np, int32_t L, int32_t P, float* profile,
+                                 const scd_opts* opts) {
+  scd_status s = check_fam_grid(S, Np, L, P, profile);
+  if (s != SCD_OK) return s;
+  const scd_opts& o = opts_or_default(opts);
+  return run_one(o, [&](cudaStream_t st) {
+    return scd::fam_alpha_profile((const float2*)S, Np, L, P, o.map_power, o.conjugate != 0, profile, st);
+  });
+}
+
+scd_status scd_ssca_alpha_profile(const void* S, int64_t N, int32_t Np, float* profile, const scd_opts* opts) {
+  scd_status s = check_ssca_grid(S, N, Np, profile);
+  if (s != SCD_OK) return s;
+  const scd_opts& o = opts_or_default(opts);
+  return run_one(o, [&](cudaStream_t st) {
+    return scd::ssca_alpha_profile((const float2*)S, N, Np, o.map_power, profile, st);
+  });
+}
+
+scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts) {
+  scd_status s = check_ssca_grid(S, N, Np, map);
+  if (s != SCD_OK) return s;
+  const scd_opts& o = opts_or_default(opts);
+  return run_one(o, [&](cudaStream_t st) { return scd::ssca_map((const float2*)S, N, Np, o.map_power, map, st); });
 }
 
 scd_status scd_prepare(int32_t estimator, int64_t N, int32_t Np, int32_t P) {
@@ -226,6 +288,7 @@ scd_status run_host(const void* x_host, int64_t N, int32_t Np, const float* wind
                     size_t out_bytes, size_t need, const scd_opts* opts, Run run) {
   if (!x_host || !out_host) return SCD_ERR_ARG;
   const scd_opts& o = opts_or_default(opts);
+  if (o.y) return SCD_ERR_ARG;                                 // no host form of the cross estimate
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 256)) return SCD_ERR_ARG;
   char* base = (char*)o.workspace;
@@ -346,6 +409,6 @@ const char* scd_status_string(scd_status s) {
 
 const char* scd_last_error(void) { return g_last_error; }
 
-int32_t scd_version(void) { return 100; }
+int32_t scd_version(void) { return 200; }
 
 }  // extern "C"

@@ -52,6 +52,8 @@ struct BatchArgs {
   int64_t total;                          // tiles in the whole plan
   unsigned* counters;                     // [0]: next tile, [1 + t]: tiles of task t done
   const float2* x;                        // x arena
+  const float2* y;                        // SSCA: second factor's arena (x for the auto estimate)
+  int32_t conj, pad_;                     // SSCA: 1 = conjugate estimate (y unconjugated)
   float2* out;                            // output arena
   float2* ws;                             // workspace arena
   const float* window;
@@ -149,7 +151,7 @@ __device__ __forceinline__ void fam_tile(const BatchArgs& A, const Task& t, int6
     load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
     float2* out = A.out + t.out_off;
     switch (t.P) {
-#define SCD_PR(PV) case PV: fam_pairs_tile<PV, TC>(sm, ctx, X, A.Np, out, t.tw, tile * TileShape<PV>::C); break;
+#define SCD_PR(PV) case PV: fam_pairs_tile<PV, TC>(sm, ctx, X, X, A.Np, out, t.tw, tile * TileShape<PV>::C); break;
       SCD_PR(2) SCD_PR(4) SCD_PR(8) SCD_PR(16) SCD_PR(32) SCD_PR(64) SCD_PR(128) SCD_PR(256) SCD_PR(512)
       SCD_PR(1024) SCD_PR(2048) SCD_PR(4096) SCD_PR(8192)
 #undef SCD_PR
@@ -165,7 +167,7 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
   if (t.op == OP_SSCA_CDP) {
     load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
     switch (A.Np) {
-#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, t.N, A.window, A.wnp, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
+#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, A.y + t.x_off, A.conj != 0, t.N, A.window, A.wnp, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
       SCD_CD(16) SCD_CD(32) SCD_CD(64) SCD_CD(128) SCD_CD(256)
 #undef SCD_CD
     }
@@ -622,7 +624,8 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   cudaStream_t st = (cudaStream_t)stream;
   BatchArgs A;
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = p->Np; A.L = p->L; A.total = p->total;
-  A.counters = p->d_counters; A.x = (const float2*)x_arena; A.out = (float2*)out_arena; A.ws = (float2*)workspace;
+  A.counters = p->d_counters; A.x = (const float2*)x_arena; A.y = A.x; A.conj = 0; A.pad_ = 0;
+  A.out = (float2*)out_arena; A.ws = (float2*)workspace;
   A.window = w; A.wnp = p->wnp; A.tw_np = p->tw_np; A.bmats_np = p->bm_np; A.bbytes_np = p->bbytes_np; A.err = p->err;
   const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
   const size_t cbytes = sizeof(unsigned) * (p->tasks.size() + 1);
@@ -735,9 +738,9 @@ size_t ssca_persistent_workspace(int64_t N, int Np) {
   return up256(data) + up256(sizeof(unsigned) * (ntasks + 1));
 }
 
-scd_status ssca_persistent_tuned(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
-                                 size_t ws_bytes, cudaStream_t st, int precision, int64_t item_bytes,
-                                 int64_t slot_bytes) {
+scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
+                                 float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision,
+                                 int64_t item_bytes, int64_t slot_bytes) {
   cudaError_t e = cudaSuccess;
   scd_status s = SCD_OK;
   scd_batch_plan* p = single_plan(N, Np, precision, item_bytes, slot_bytes, &e, &s);
@@ -751,7 +754,8 @@ scd_status ssca_persistent_tuned(const float2* x, int64_t N, int Np, const float
   unsigned* counters = (unsigned*)((char*)ws + data);
   BatchArgs A;
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = Np; A.L = 1; A.total = p->total;
-  A.counters = counters; A.x = x; A.out = out; A.ws = (float2*)ws;
+  A.counters = counters; A.x = x; A.y = y ? y : x; A.conj = conj ? 1 : 0; A.pad_ = 0;
+  A.out = out; A.ws = (float2*)ws;
   A.window = window ? window : p->hamming; A.wnp = p->wnp; A.tw_np = p->tw_np; A.bmats_np = p->bm_np;
   A.bbytes_np = p->bbytes_np; A.err = p->err;
   count_launches(1);
@@ -760,9 +764,9 @@ scd_status ssca_persistent_tuned(const float2* x, int64_t N, int Np, const float
   return e == cudaSuccess ? SCD_OK : cuda_status(e);
 }
 
-scd_status ssca_persistent(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
-                           size_t ws_bytes, cudaStream_t st, int precision) {
-  return ssca_persistent_tuned(x, N, Np, window, out, ws, ws_bytes, st, precision, kItemBytes, kSlotBytes);
+scd_status ssca_persistent(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
+                           float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision) {
+  return ssca_persistent_tuned(x, y, conj, N, Np, window, out, ws, ws_bytes, st, precision, kItemBytes, kSlotBytes);
 }
 
 TuneEntry ssca_auto_choice(int64_t N, int Np, int precision) {
@@ -798,8 +802,8 @@ extern "C" scd_status scd_ssca_tune(const void* x, int64_t N, int32_t Np, const 
   for (int64_t item : items)
     for (int64_t slot : slots) {
       s = time_candidate(st, reps, [&]() {
-        return ssca_persistent_tuned((const float2*)x, N, Np, window, (float2*)out, o.workspace, o.workspace_bytes, st,
-                                     o.precision, item, slot);
+        return ssca_persistent_tuned((const float2*)x, (const float2*)o.y, o.conjugate != 0, N, Np, window,
+                                     (float2*)out, o.workspace, o.workspace_bytes, st, o.precision, item, slot);
       }, &ms);
       if (s != SCD_OK) return s;
       if (ms < best.ms) best = TuneEntry{SCD_SCHEDULE_PERSISTENT, item, slot, ms};

@@ -31,12 +31,13 @@ cudaError_t build_pass_into(float2* out, int M, cudaStream_t st);   // PlanInfo<
 cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st);
 
 // ---------------------------------------------------------------- FAM (fam.cu)
-// X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL + n] W_Np^{(k n) mod Np}
+// X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL + n] W_Np^{(k n) mod Np}  (conj(X) if conj_out)
 // precision: SCD_FP32 or SCD_SPLIT_BF16 (radix DFTs as bf16 hi/lo tensor-core GEMMs)
 cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* window, float2* X,
-                           cudaStream_t st, int precision);
-// out[kh][lh][qh] = sum_p X[kh][p] conj(X[lh][p]) W_P^{(q p) mod P}
-cudaError_t fam_pair_fft(const float2* X, int Np, int P, float2* out, cudaStream_t st, int precision);
+                           cudaStream_t st, int precision, bool conj_out = false);
+// out[kh][lh][qh] = sum_p X[kh][p] conj(Y[lh][p]) W_P^{(q p) mod P}   (Y = X: auto estimate)
+cudaError_t fam_pair_fft(const float2* X, const float2* Y, int Np, int P, float2* out, cudaStream_t st,
+                         int precision);
 // The same two kernels with caller-provided tables (W_Np roots, pass twiddles of size Np
 // and of size P) instead of the cached ones.
 cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
@@ -46,9 +47,9 @@ cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const
 // ---------------------------------------------------------------- SSCA (ssca.cu)
 void ssca_split(int64_t N, int* M1, int* M2);
 int ssca_cols_per_tile(int M1);    // columns m2 per CTA of the column pass (256 threads)
-// Stage 0: channeliser + CDP, X_g into ws[kh][n]
-cudaError_t ssca_cdp(const float2* x, int64_t N, int Np, const float* window, float2* ws, cudaStream_t st,
-                     int precision);
+// Stage 0: channeliser + CDP, X_g into ws[kh][n]: X_T(n,k) conj(y[n]) (y[n] if conj)
+cudaError_t ssca_cdp(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window, float2* ws,
+                     cudaStream_t st, int precision);
 // Stage 1: M1-point column FFTs times the rotate factor, in place on ws
 cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st, int precision);
 // Stage 2: M2-point row FFTs, fftshifted into out[kh][sh]
@@ -56,13 +57,18 @@ cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStre
 
 // Default schedule of scd_ssca: one persistent launch (batch.cu) over a cached one-signal plan.
 size_t ssca_persistent_workspace(int64_t N, int Np);
-scd_status ssca_persistent(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
-                           size_t ws_bytes, cudaStream_t st, int precision);
+// y, conj: the channel-data product's second factor, as ssca_cdp
+scd_status ssca_persistent(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
+                           float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision);
 void release_single_plans();
 
 // ---------------------------------------------------------------- maps (map.cu)
-cudaError_t fam_map(const float2* S, int Np, int L, int P, int power, float* map, cudaStream_t st);
+cudaError_t fam_map(const float2* S, int Np, int L, int P, int power, bool conj, float* map, cudaStream_t st);
 cudaError_t ssca_map(const float2* S, int64_t N, int Np, int power, float* map, cudaStream_t st);
+// alpha profiles: the largest |S|^power over f of every alpha column of the maps above
+cudaError_t fam_alpha_profile(const float2* S, int Np, int L, int P, int power, bool conj, float* prof,
+                              cudaStream_t st);
+cudaError_t ssca_alpha_profile(const float2* S, int64_t N, int Np, int power, float* prof, cudaStream_t st);
 
 // ---------------------------------------------------------------- autotuner cache (tune.cu)
 struct TuneEntry {
@@ -76,9 +82,9 @@ bool tune_lookup(const std::string& key, TuneEntry* out);
 void tune_store(const std::string& key, const TuneEntry& e);
 // scd_ssca under SCD_SCHEDULE_AUTO: the tuned choice, else the default (STAGES)
 TuneEntry ssca_auto_choice(int64_t N, int Np, int precision);
-scd_status ssca_persistent_tuned(const float2* x, int64_t N, int Np, const float* window, float2* out, void* ws,
-                                 size_t ws_bytes, cudaStream_t st, int precision, int64_t item_bytes,
-                                 int64_t slot_bytes);
+scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
+                                 float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision,
+                                 int64_t item_bytes, int64_t slot_bytes);
 
 // ---------------------------------------------------------------- launch accounting
 void count_launches(int n);

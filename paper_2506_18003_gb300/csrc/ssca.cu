@@ -3,7 +3,9 @@
 //
 // K3: Sec. II-C with the complex demodulate of Sec. II-A (Eq. II.A-complex demodulate)
 //     centred on n: window, Np-point FFT, down-conversion W_Np^{(k s) mod Np} and the
-//     product with conj(x[n]) (Eq. Xg), all in the FFT's output stage.  Writes
+//     product with conj(y[n]) (Eq. Xg; y = x for the auto estimate, the second signal of a
+//     cross estimate, or y[n] unconjugated for a conjugate one), all in the FFT's output
+//     stage.  Writes
 //     X_g[kh][n] (channel-major, n contiguous).
 // K4a: Stage 1 of Sec. III-B-1 (Eq. Chap4_2DFFT, "M1-point DFT on the m2-th column" times
 //     the rotate factor W_N^{(m2 m1') mod N}), in place on X_g viewed as [kh][m1][m2] with
@@ -21,16 +23,16 @@ namespace {
 
 template <int NP, bool TC>
 __global__ void __launch_bounds__(TileShape<NP>::NT)
-k_ssca_cdp(const float2* __restrict__ x, int N, const float* __restrict__ a, const float2* __restrict__ wnp,
-           const float2* __restrict__ tw, float2* __restrict__ Xg, const unsigned char* __restrict__ bmats,
-           unsigned* err) {
+k_ssca_cdp(const float2* __restrict__ x, const float2* __restrict__ y, int conj, int N, const float* __restrict__ a,
+           const float2* __restrict__ wnp, const float2* __restrict__ tw, float2* __restrict__ Xg,
+           const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<NP>;
   using FS = FftSmem<NP, S::C, S::NT, TC>;
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  ssca_cdp_tile<NP, TC>(sm, ctx, x, N, a, wnp, tw, Xg, blockIdx.x * S::C);
+  ssca_cdp_tile<NP, TC>(sm, ctx, x, y, conj != 0, N, a, wnp, tw, Xg, blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
@@ -85,13 +87,13 @@ cudaError_t tc_args(bool tc, int M, TcArgs* a) {
 }
 
 template <int NPV, bool TC>
-cudaError_t launch_cdp_t(const float2* x, int N, const float* a, const float2* wnp, const float2* tw, float2* Xg,
-                         TcArgs t, cudaStream_t st) {
+cudaError_t launch_cdp_t(const float2* x, const float2* y, int conj, int N, const float* a, const float2* wnp,
+                         const float2* tw, float2* Xg, TcArgs t, cudaStream_t st) {
   using S = TileShape<NPV>;
   constexpr int sm = FftSmem<NPV, S::C, S::NT, TC>::total;
   cudaError_t e = set_smem(k_ssca_cdp<NPV, TC>, sm);
   if (e != cudaSuccess) return e;
-  k_ssca_cdp<NPV, TC><<<N / S::C, S::NT, sm, st>>>(x, N, a, wnp, tw, Xg, t.bm, t.err);
+  k_ssca_cdp<NPV, TC><<<N / S::C, S::NT, sm, st>>>(x, y, conj, N, a, wnp, tw, Xg, t.bm, t.err);
   return cudaGetLastError();
 }
 
@@ -123,7 +125,8 @@ cudaError_t launch_rows_t(const float2* Y, int N, int Np, int M1, int M2, float2
   return cudaGetLastError();
 }
 
-cudaError_t launch_cdp(const float2* x, int N, int Np, const float* a, float2* Xg, bool tc, cudaStream_t st) {
+cudaError_t launch_cdp(const float2* x, const float2* y, int conj, int N, int Np, const float* a, float2* Xg, bool tc,
+                       cudaStream_t st) {
   cudaError_t err;
   const float2* wnp = table_roots(Np, &err);
   if (!wnp) return err;
@@ -131,8 +134,8 @@ cudaError_t launch_cdp(const float2* x, int N, int Np, const float* a, float2* X
   if (!tw) return err;
   TcArgs t;
   if ((err = tc_args(tc, Np, &t)) != cudaSuccess) return err;
-#define SCD_K3(NPV) return tc ? launch_cdp_t<NPV, true>(x, N, a, wnp, tw, Xg, t, st) \
-                              : launch_cdp_t<NPV, false>(x, N, a, wnp, tw, Xg, t, st)
+#define SCD_K3(NPV) return tc ? launch_cdp_t<NPV, true>(x, y, conj, N, a, wnp, tw, Xg, t, st) \
+                              : launch_cdp_t<NPV, false>(x, y, conj, N, a, wnp, tw, Xg, t, st)
   switch (Np) {
     case 16: SCD_K3(16);
     case 32: SCD_K3(32);
@@ -197,10 +200,10 @@ void ssca_split(int64_t N, int* M1, int* M2) {
   *M2 = 1 << (e / 2);
 }
 
-cudaError_t ssca_cdp(const float2* x, int64_t N, int Np, const float* window, float2* ws, cudaStream_t st,
-                     int precision) {
+cudaError_t ssca_cdp(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window, float2* ws,
+                     cudaStream_t st, int precision) {
   count_launches(1);
-  return launch_cdp(x, (int)N, Np, window, ws, precision == SCD_SPLIT_BF16, st);
+  return launch_cdp(x, y, conj ? 1 : 0, (int)N, Np, window, ws, precision == SCD_SPLIT_BF16, st);
 }
 
 cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st, int precision) {

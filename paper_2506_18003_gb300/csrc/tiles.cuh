@@ -25,10 +25,12 @@ __device__ __forceinline__ void tile_fft(float2* sm, const float2* __restrict__ 
 
 // ---------------------------------------------------------------- FAM channeliser (K1)
 // frames p0 .. p0 + C - 1:  X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL+n] W_Np^{(k n) mod Np}
+// (conj_out: conj(X) is stored instead, the second operand of a conjugate estimate)
 template <int NP, bool TC>
 __device__ __forceinline__ void fam_channelise_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x, int L, int P,
                                                     const float* __restrict__ a, const float2* __restrict__ wnp,
-                                                    const float2* __restrict__ tw, float2* __restrict__ X, int p0) {
+                                                    const float2* __restrict__ tw, float2* __restrict__ X, int p0,
+                                                    bool conj_out = false) {
   using S = TileShape<NP>;
   auto src = [&](int c, int n) -> float2 {
     const int p = p0 + c;
@@ -40,24 +42,29 @@ __device__ __forceinline__ void fam_channelise_tile(float2* sm, TcCtx& ctx, cons
     if (p >= P) return;
     const int pl = (int)(((int64_t)p * L) & (NP - 1));          // (p L) mod Np
     const int kh = (f + NP / 2) & (NP - 1);
-    X[(int64_t)kh * P + p] = cmul(v, __ldg(wnp + ((f * pl) & (NP - 1))));
+    float2 r = cmul(v, __ldg(wnp + ((f * pl) & (NP - 1))));
+    if (conj_out) r.y = -r.y;
+    X[(int64_t)kh * P + p] = r;
   };
   tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
 
 // ---------------------------------------------------------------- FAM pair FFT (K2)
 // pairs pair0 .. pair0 + C - 1 (pair = kh Np + lh):
-//   out[kh][lh][qh] = sum_p X[kh][p] conj(X[lh][p]) W_P^{(q p) mod P}
+//   out[kh][lh][qh] = sum_p X[kh][p] conj(Y[lh][p]) W_P^{(q p) mod P}
+// Y = X for the auto estimate, the partner's channeliser output for a cross estimate, and
+// the conjugated one for a conjugate estimate.
 template <int PP, bool TC>
-__device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X, int Np,
-                                               float2* __restrict__ out, const float2* __restrict__ tw, int64_t pair0) {
+__device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X,
+                                               const float2* __restrict__ Y, int Np, float2* __restrict__ out,
+                                               const float2* __restrict__ tw, int64_t pair0) {
   using S = TileShape<PP>;
   // this thread's pair (transforms are t-fast: c = tid / T), resolved once
   const int64_t pair = pair0 + (int)threadIdx.x / S::T;
   const bool valid = pair < (int64_t)Np * Np;
   const int kh = valid ? (int)(pair / Np) : 0, lh = valid ? (int)(pair % Np) : 0;
   const float2* __restrict__ xk = X + (int64_t)kh * PP;
-  const float2* __restrict__ xl = X + (int64_t)lh * PP;
+  const float2* __restrict__ xl = Y + (int64_t)lh * PP;
   float2* __restrict__ o = out + pair * PP;
   auto src = [&](int, int p) -> float2 {
     return valid ? cmulc(__ldg(xk + p), __ldg(xl + p)) : make_float2(0.f, 0.f);
@@ -69,9 +76,11 @@ __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const flo
 }
 
 // ---------------------------------------------------------------- SSCA channeliser + CDP (K3)
-// time points n0 .. n0 + C - 1:  X_g[kh][n] = W_Np^{(k s) mod Np} DFT_Np(a x[s ..])[k] conj(x[n])
+// time points n0 .. n0 + C - 1:  X_g[kh][n] = W_Np^{(k s) mod Np} DFT_Np(a x[s ..])[k] conj(y[n])
+// (y = x for the auto estimate; conj: y[n] itself, the conjugate estimate)
 template <int NP, bool TC>
-__device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x, int N,
+__device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x,
+                                              const float2* __restrict__ y, bool conj, int N,
                                               const float* __restrict__ a, const float2* __restrict__ wnp,
                                               const float2* __restrict__ tw, float2* __restrict__ Xg, int n0) {
   using S = TileShape<NP>;
@@ -79,7 +88,8 @@ __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const floa
   const int n = n0 + (int)threadIdx.x % S::C;
   const bool interior = n0 - NP / 2 >= 0 && n0 + S::C + NP / 2 <= N;   // whole tile away from the ends
   const float2* __restrict__ xb = x + (n - NP / 2);
-  const float2 xn = __ldg(x + n);
+  float2 xn = __ldg(y + n);                                        // the factor is conj(xn)
+  if (conj) xn.y = -xn.y;
   const int s = (n - NP / 2) & (NP - 1);                            // s mod Np (s may be < 0)
   float2* __restrict__ o = Xg + n;
   auto src = [&](int, int r) -> float2 {

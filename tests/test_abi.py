@@ -3,6 +3,7 @@ arguments synchronously (these checks run before any CUDA call, so no GPU is nee
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -42,7 +43,7 @@ def test_status_strings(lib):
 
 
 def test_workspace_queries(lib):
-    assert lib.scd_fam_workspace_bytes(65728, 256, 64, 1024, 0) == 256 * 1024 * 8
+    assert lib.scd_fam_workspace_bytes(65728, 256, 64, 1024, 0) == 2 * 256 * 1024 * 8   # X and Y
     assert lib.scd_ssca_workspace_bytes(1 << 20, 256, 0) >= 256 * (1 << 20) * 8
     assert lib.scd_fam_workspace_bytes(280, 32, 8, 32, 0) % 256 == 0
 
@@ -102,3 +103,49 @@ def test_map_validation(lib):
     assert lib.scd_fam_map(FAKE, 32, 8, 32, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
     assert lib.scd_fam_map(FAKE, 32, 20, 32, FAKE, None) == binding.SCD_ERR_UNSUPPORTED   # 2L > Np
     assert lib.scd_fam_map(FAKE, 32, 3, 8, FAKE, None) == binding.SCD_ERR_UNSUPPORTED     # PL % Np
+
+
+def test_variant_validation(lib):
+    o = binding.ScdOpts()
+    o.map_power = 1
+    o.workspace = 1 << 20
+    o.workspace_bytes = 1 << 40
+    o.y = (1 << 20) + 4                                  # misaligned second signal
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    assert lib.scd_ssca(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    o.y = None
+    o.conjugate = 2                                      # not 0 / 1
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    assert lib.scd_ssca(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    o.conjugate = 1
+    assert lib.scd_fam_noalloc(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_UNSUPPORTED
+    o.conjugate = 0
+    o.y = 1 << 20                                        # host variants take no second signal
+    assert lib.scd_fam_host(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    assert lib.scd_ssca_host(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+
+
+def test_profile_validation(lib):
+    assert lib.scd_fam_alpha_profile(None, 32, 8, 32, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_fam_alpha_profile(FAKE, 32, 20, 32, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+    assert lib.scd_ssca_alpha_profile(FAKE, 4096, 32, None, None) == binding.SCD_ERR_ARG
+    assert lib.scd_ssca_alpha_profile(FAKE, 5000, 32, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+    o = binding.ScdOpts()
+    o.map_power = 0
+    assert lib.scd_ssca_alpha_profile(FAKE, 4096, 32, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+
+
+def test_opts_layout_matches_header(tmp_path):
+    """The ctypes mirror of scd_opts has the C struct's size and field offsets (a C
+    program compiled against include/scd.h prints them)."""
+    fields = [f for f, _ in binding.ScdOpts._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"scd.h\"\nint main(void) {\n"
+                   + f'  printf("%zu\\n", sizeof(scd_opts));\n'
+                   + "".join(f'  printf("%zu\\n", offsetof(scd_opts, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(binding.ScdOpts)] + [getattr(binding.ScdOpts, f).offset for f in fields]
+    assert got == want
