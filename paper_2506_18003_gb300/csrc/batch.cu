@@ -57,7 +57,6 @@ struct BatchArgs {
   float2* out;                            // output arena
   float2* ws;                             // workspace arena
   const float* window;
-  const float2* wnp;                      // W_Np roots
   const float2* tw_np;                    // pass twiddles of size Np
   const unsigned char* bmats_np;          // split form: B matrices of size Np
   int32_t bbytes_np;
@@ -143,7 +142,7 @@ __device__ __forceinline__ void fam_tile(const BatchArgs& A, const Task& t, int6
   if (t.op == OP_FAM_CHAN) {
     load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
     switch (A.Np) {
-#define SCD_CH(NPV) case NPV: fam_channelise_tile<NPV, TC>(sm, ctx, x, A.L, t.P, A.window, A.wnp, A.tw_np, X, (int)tile * TileShape<NPV>::C); break;
+#define SCD_CH(NPV) case NPV: fam_channelise_tile<NPV, TC>(sm, ctx, x, A.L, t.P, A.window, A.tw_np, X, (int)tile * TileShape<NPV>::C); break;
       SCD_CH(16) SCD_CH(32) SCD_CH(64) SCD_CH(128) SCD_CH(256)
 #undef SCD_CH
     }
@@ -167,7 +166,7 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
   if (t.op == OP_SSCA_CDP) {
     load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
     switch (A.Np) {
-#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, A.y + t.x_off, A.conj != 0, t.N, A.window, A.wnp, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
+#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, A.y + t.x_off, A.conj != 0, t.N, A.window, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
       SCD_CD(16) SCD_CD(32) SCD_CD(64) SCD_CD(128) SCD_CD(256)
 #undef SCD_CD
     }
@@ -325,7 +324,6 @@ struct scd_batch_plan {
   int64_t total = 0;
   size_t ws_bytes = 0;
   int grid = 0, smem = 0;
-  const float2* wnp = nullptr;
   const float2* tw_np = nullptr;
   const unsigned char* bm_np = nullptr;
   int bbytes_np = 0;
@@ -561,7 +559,7 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     p->ws_off[i + 1] = p->ws_off[i] + (int64_t)Np * sz;
   }
   // tables
-  if (!(p->wnp = table_roots(Np, &e)) || !(p->tw_np = table_pass(Np, &e)) || !(p->hamming = table_hamming(Np, &e)) ||
+  if (!(p->tw_np = table_pass(Np, &e)) || !(p->hamming = table_hamming(Np, &e)) ||
       !(p->err = device_error_word(&e))) {
     free_plan(p);
     return cuda_status(e);
@@ -626,7 +624,7 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = p->Np; A.L = p->L; A.total = p->total;
   A.counters = p->d_counters; A.x = (const float2*)x_arena; A.y = A.x; A.conj = 0; A.pad_ = 0;
   A.out = (float2*)out_arena; A.ws = (float2*)workspace;
-  A.window = w; A.wnp = p->wnp; A.tw_np = p->tw_np; A.bmats_np = p->bm_np; A.bbytes_np = p->bbytes_np; A.err = p->err;
+  A.window = w; A.tw_np = p->tw_np; A.bmats_np = p->bm_np; A.bbytes_np = p->bbytes_np; A.err = p->err;
   const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
   const size_t cbytes = sizeof(unsigned) * (p->tasks.size() + 1);
   count_launches(1);
@@ -756,7 +754,7 @@ scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, in
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = Np; A.L = 1; A.total = p->total;
   A.counters = counters; A.x = x; A.y = y ? y : x; A.conj = conj ? 1 : 0; A.pad_ = 0;
   A.out = out; A.ws = (float2*)ws;
-  A.window = window ? window : p->hamming; A.wnp = p->wnp; A.tw_np = p->tw_np; A.bmats_np = p->bm_np;
+  A.window = window ? window : p->hamming; A.tw_np = p->tw_np; A.bmats_np = p->bm_np;
   A.bbytes_np = p->bbytes_np; A.err = p->err;
   count_launches(1);
   if ((e = cudaMemsetAsync(counters, 0, cbytes, st)) != cudaSuccess) return cuda_status(e);

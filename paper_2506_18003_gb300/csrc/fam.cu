@@ -3,8 +3,8 @@
 // tensor-core GEMMs with FP32 accumulation, fft_tc.cuh).
 //
 // K1 implements Eq. II.B-complex_demodulate_final with the block framing of Algorithm 1
-// (`Framing`, `Demodulate`): window, Np-point FFT, down-conversion W_Np^{(k p L) mod Np}
-// fused into the FFT's output stage.  It writes X[kh][p] (P contiguous per channel), the
+// (`Framing`, `Demodulate`): window, Np-point FFT and the down-conversion W_Np^{(k p L) mod Np},
+// which is folded into the FFT by rotating each frame's input by (p L) mod Np positions.  It writes X[kh][p] (P contiguous per channel), the
 // layout the pair stage reads rows from.
 //
 // K2 implements Eq. II.B-SCD_function_FAM (Algorithm 1, `FFT2`): for every channel pair the
@@ -23,7 +23,7 @@ namespace {
 template <int NP, bool TC>
 __global__ void __launch_bounds__(TileShape<NP>::NT)
 k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __restrict__ a,
-                 const float2* __restrict__ wnp, const float2* __restrict__ tw, float2* __restrict__ X,
+                 const float2* __restrict__ tw, float2* __restrict__ X,
                  const unsigned char* __restrict__ bmats, unsigned* err, int conj_out) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<NP>;
@@ -31,7 +31,7 @@ k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __rest
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  fam_channelise_tile<NP, TC>(sm, ctx, x, L, P, a, wnp, tw, X, blockIdx.x * S::C, conj_out != 0);
+  fam_channelise_tile<NP, TC>(sm, ctx, x, L, P, a, tw, X, blockIdx.x * S::C, conj_out != 0);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
@@ -56,13 +56,13 @@ cudaError_t set_smem(K kernel, int bytes) {
 }
 
 template <int NPV, bool TC>
-cudaError_t launch_k1(const float2* x, int L, int P, const float* window, const float2* wnp, const float2* tw,
+cudaError_t launch_k1(const float2* x, int L, int P, const float* window, const float2* tw,
                       float2* X, const unsigned char* bm, unsigned* err, int conj_out, cudaStream_t st) {
   using S = TileShape<NPV>;
   constexpr int sm = FftSmem<NPV, S::C, S::NT, TC>::total;
   cudaError_t e = set_smem(k_fam_channelise<NPV, TC>, sm);
   if (e != cudaSuccess) return e;
-  k_fam_channelise<NPV, TC><<<(P + S::C - 1) / S::C, S::NT, sm, st>>>(x, L, P, window, wnp, tw, X, bm, err, conj_out);
+  k_fam_channelise<NPV, TC><<<(P + S::C - 1) / S::C, S::NT, sm, st>>>(x, L, P, window, tw, X, bm, err, conj_out);
   return cudaGetLastError();
 }
 
@@ -79,15 +79,14 @@ cudaError_t launch_k2(const float2* X, const float2* Y, int Np, float2* out, con
 }
 
 template <bool TC>
-cudaError_t dispatch_k1(int Np, const float2* x, int L, int P, const float* window, const float2* wnp,
-                        const float2* tw, float2* X, const unsigned char* bm, unsigned* err, int conj_out,
+cudaError_t dispatch_k1(int Np, const float2* x, int L, int P, const float* window, const float2* tw, float2* X, const unsigned char* bm, unsigned* err, int conj_out,
                         cudaStream_t st) {
   switch (Np) {
-    case 16: return launch_k1<16, TC>(x, L, P, window, wnp, tw, X, bm, err, conj_out, st);
-    case 32: return launch_k1<32, TC>(x, L, P, window, wnp, tw, X, bm, err, conj_out, st);
-    case 64: return launch_k1<64, TC>(x, L, P, window, wnp, tw, X, bm, err, conj_out, st);
-    case 128: return launch_k1<128, TC>(x, L, P, window, wnp, tw, X, bm, err, conj_out, st);
-    case 256: return launch_k1<256, TC>(x, L, P, window, wnp, tw, X, bm, err, conj_out, st);
+    case 16: return launch_k1<16, TC>(x, L, P, window, tw, X, bm, err, conj_out, st);
+    case 32: return launch_k1<32, TC>(x, L, P, window, tw, X, bm, err, conj_out, st);
+    case 64: return launch_k1<64, TC>(x, L, P, window, tw, X, bm, err, conj_out, st);
+    case 128: return launch_k1<128, TC>(x, L, P, window, tw, X, bm, err, conj_out, st);
+    case 256: return launch_k1<256, TC>(x, L, P, window, tw, X, bm, err, conj_out, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -128,8 +127,6 @@ cudaError_t tc_tables(int M, const unsigned char** bm, unsigned** ew) {
 cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* window, float2* X, cudaStream_t st,
                            int precision, bool conj_out) {
   cudaError_t err;
-  const float2* wnp = table_roots(Np, &err);
-  if (!wnp) return err;
   const float2* tw = table_pass(Np, &err);
   if (!tw) return err;
   count_launches(1);
@@ -137,9 +134,9 @@ cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* w
     const unsigned char* bm;
     unsigned* ew;
     if ((err = tc_tables(Np, &bm, &ew)) != cudaSuccess) return err;
-    return dispatch_k1<true>(Np, x, L, P, window, wnp, tw, X, bm, ew, conj_out, st);
+    return dispatch_k1<true>(Np, x, L, P, window, tw, X, bm, ew, conj_out, st);
   }
-  return dispatch_k1<false>(Np, x, L, P, window, wnp, tw, X, nullptr, nullptr, conj_out, st);
+  return dispatch_k1<false>(Np, x, L, P, window, tw, X, nullptr, nullptr, conj_out, st);
 }
 
 cudaError_t fam_pair_fft(const float2* X, const float2* Y, int Np, int P, float2* out, cudaStream_t st, int precision) {
@@ -157,9 +154,9 @@ cudaError_t fam_pair_fft(const float2* X, const float2* Y, int Np, int P, float2
 }
 
 cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
-                                const float2* wnp, const float2* tw, cudaStream_t st) {
+                                const float2* tw, cudaStream_t st) {
   count_launches(1);
-  return dispatch_k1<false>(Np, x, L, P, window, wnp, tw, X, nullptr, nullptr, 0, st);
+  return dispatch_k1<false>(Np, x, L, P, window, tw, X, nullptr, nullptr, 0, st);
 }
 
 cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const float2* tw, cudaStream_t st) {

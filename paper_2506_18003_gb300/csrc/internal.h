@@ -26,7 +26,6 @@ unsigned* device_error_word(cudaError_t* err);
 void release_tables();
 // The same FP64 builders, writing into memory the caller provides (no allocation, no
 // synchronisation; enqueued on st).
-cudaError_t build_roots_into(float2* out, int M, cudaStream_t st);
 cudaError_t build_pass_into(float2* out, int M, cudaStream_t st);   // PlanInfo<M>::tw_len() entries
 cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st);
 
@@ -38,10 +37,10 @@ cudaError_t fam_channelise(const float2* x, int Np, int L, int P, const float* w
 // out[kh][lh][qh] = sum_p X[kh][p] conj(Y[lh][p]) W_P^{(q p) mod P}   (Y = X: auto estimate)
 cudaError_t fam_pair_fft(const float2* X, const float2* Y, int Np, int P, float2* out, cudaStream_t st,
                          int precision);
-// The same two kernels with caller-provided tables (W_Np roots, pass twiddles of size Np
-// and of size P) instead of the cached ones.
+// The same two kernels with caller-provided tables (pass twiddles of size Np and of size P)
+// instead of the cached ones.
 cudaError_t fam_channelise_with(const float2* x, int Np, int L, int P, const float* window, float2* X,
-                                const float2* wnp, const float2* tw_np, cudaStream_t st);
+                                const float2* tw_np, cudaStream_t st);
 cudaError_t fam_pair_fft_with(const float2* X, int Np, int P, float2* out, const float2* tw_p, cudaStream_t st);
 
 // ---------------------------------------------------------------- SSCA (ssca.cu)

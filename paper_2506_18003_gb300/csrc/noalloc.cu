@@ -32,9 +32,9 @@
 namespace {
 
 constexpr int64_t kNoallocMaxX = 1 << 18;                  // complex elements of X
-// table region: W_Np (<= 256), pass table of Np (<= 256), pass table of P (<= 17408),
-// Hamming window (256 float = 128 float2)
-constexpr int64_t kTabRoots = 0, kTabPassNp = 256, kTabPassP = 512, kTabWindow = 512 + 17408;
+// table region: pass table of Np (<= 256), pass table of P (<= 17408), Hamming window
+// (256 float = 128 float2)
+constexpr int64_t kTabPassNp = 0, kTabPassP = 256, kTabWindow = 256 + 17408;
 constexpr int64_t kTabLen = kTabWindow + 128;
 constexpr int64_t kScratchLen = kNoallocMaxX + kTabLen;     // float2 elements
 
@@ -87,18 +87,16 @@ scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t L, int3
   cudaError_t e = scratch_address(&base);
   if (e == cudaSuccess) {
     float2* tab = base + kNoallocMaxX;
-    float2* wnp = tab + kTabRoots;
     float2* tw_np = tab + kTabPassNp;
     float2* tw_p = tab + kTabPassP;
     if (!window) {
       float* w = (float*)(tab + kTabWindow);
       if ((e = scd::build_hamming_into(w, Np, st)) == cudaSuccess) window = w;
     }
-    if (e == cudaSuccess) e = scd::build_roots_into(wnp, Np, st);
     if (e == cudaSuccess) e = scd::build_pass_into(tw_np, Np, st);
     if (e == cudaSuccess) e = scd::build_pass_into(tw_p, P, st);
     if (e == cudaSuccess)
-      e = scd::fam_channelise_with((const float2*)x, Np, L, P, window, base, wnp, tw_np, st);
+      e = scd::fam_channelise_with((const float2*)x, Np, L, P, window, base, tw_np, st);
     if (e == cudaSuccess) e = scd::fam_pair_fft_with(base, Np, P, (float2*)out, tw_p, st);
   }
   if (e != cudaSuccess) {

@@ -2,7 +2,8 @@
 // and K4b row pass of the decomposed N-point strip FFT.
 //
 // K3: Sec. II-C with the complex demodulate of Sec. II-A (Eq. II.A-complex demodulate)
-//     centred on n: window, Np-point FFT, down-conversion W_Np^{(k s) mod Np} and the
+//     centred on n: window, Np-point FFT, down-conversion W_Np^{(k s) mod Np} (folded into
+//     the FFT by rotating the frame's input by s mod Np positions) and the
 //     product with conj(y[n]) (Eq. Xg; y = x for the auto estimate, the second signal of a
 //     cross estimate, or y[n] unconjugated for a conjugate one), all in the FFT's output
 //     stage.  Writes
@@ -24,7 +25,7 @@ namespace {
 template <int NP, bool TC>
 __global__ void __launch_bounds__(TileShape<NP>::NT)
 k_ssca_cdp(const float2* __restrict__ x, const float2* __restrict__ y, int conj, int N, const float* __restrict__ a,
-           const float2* __restrict__ wnp, const float2* __restrict__ tw, float2* __restrict__ Xg,
+           const float2* __restrict__ tw, float2* __restrict__ Xg,
            const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<NP>;
@@ -32,7 +33,7 @@ k_ssca_cdp(const float2* __restrict__ x, const float2* __restrict__ y, int conj,
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  ssca_cdp_tile<NP, TC>(sm, ctx, x, y, conj != 0, N, a, wnp, tw, Xg, blockIdx.x * S::C);
+  ssca_cdp_tile<NP, TC>(sm, ctx, x, y, conj != 0, N, a, tw, Xg, blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
@@ -87,13 +88,12 @@ cudaError_t tc_args(bool tc, int M, TcArgs* a) {
 }
 
 template <int NPV, bool TC>
-cudaError_t launch_cdp_t(const float2* x, const float2* y, int conj, int N, const float* a, const float2* wnp,
-                         const float2* tw, float2* Xg, TcArgs t, cudaStream_t st) {
+cudaError_t launch_cdp_t(const float2* x, const float2* y, int conj, int N, const float* a, const float2* tw, float2* Xg, TcArgs t, cudaStream_t st) {
   using S = TileShape<NPV>;
   constexpr int sm = FftSmem<NPV, S::C, S::NT, TC>::total;
   cudaError_t e = set_smem(k_ssca_cdp<NPV, TC>, sm);
   if (e != cudaSuccess) return e;
-  k_ssca_cdp<NPV, TC><<<N / S::C, S::NT, sm, st>>>(x, y, conj, N, a, wnp, tw, Xg, t.bm, t.err);
+  k_ssca_cdp<NPV, TC><<<N / S::C, S::NT, sm, st>>>(x, y, conj, N, a, tw, Xg, t.bm, t.err);
   return cudaGetLastError();
 }
 
@@ -128,14 +128,12 @@ cudaError_t launch_rows_t(const float2* Y, int N, int Np, int M1, int M2, float2
 cudaError_t launch_cdp(const float2* x, const float2* y, int conj, int N, int Np, const float* a, float2* Xg, bool tc,
                        cudaStream_t st) {
   cudaError_t err;
-  const float2* wnp = table_roots(Np, &err);
-  if (!wnp) return err;
   const float2* tw = table_pass(Np, &err);
   if (!tw) return err;
   TcArgs t;
   if ((err = tc_args(tc, Np, &t)) != cudaSuccess) return err;
-#define SCD_K3(NPV) return tc ? launch_cdp_t<NPV, true>(x, y, conj, N, a, wnp, tw, Xg, t, st) \
-                              : launch_cdp_t<NPV, false>(x, y, conj, N, a, wnp, tw, Xg, t, st)
+#define SCD_K3(NPV) return tc ? launch_cdp_t<NPV, true>(x, y, conj, N, a, tw, Xg, t, st) \
+                              : launch_cdp_t<NPV, false>(x, y, conj, N, a, tw, Xg, t, st)
   switch (Np) {
     case 16: SCD_K3(16);
     case 32: SCD_K3(32);

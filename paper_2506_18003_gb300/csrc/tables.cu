@@ -154,11 +154,6 @@ const float* table_hamming(int Np, cudaError_t* err) {
   });
 }
 
-cudaError_t build_roots_into(float2* out, int M, cudaStream_t st) {
-  k_roots<<<grid_for(M), 256, 0, st>>>(out, M);
-  return cudaGetLastError();
-}
-
 cudaError_t build_pass_into(float2* out, int M, cudaStream_t st) {
   PassRadices r = pass_radices(M);
   if (r.r0 == 0) return cudaErrorInvalidValue;

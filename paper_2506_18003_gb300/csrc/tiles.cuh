@@ -25,26 +25,25 @@ __device__ __forceinline__ void tile_fft(float2* sm, const float2* __restrict__ 
 
 // ---------------------------------------------------------------- FAM channeliser (K1)
 // frames p0 .. p0 + C - 1:  X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL+n] W_Np^{(k n) mod Np}
+// The down-conversion costs nothing: the windowed sample a[n] x[pL+n] is placed at FFT input
+// position (pL + n) mod Np, so the transform itself produces sum_n a[n] x[pL+n] W_Np^{k (pL+n)}.
 // (conj_out: conj(X) is stored instead, the second operand of a conjugate estimate)
 template <int NP, bool TC>
 __device__ __forceinline__ void fam_channelise_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x, int L, int P,
-                                                    const float* __restrict__ a, const float2* __restrict__ wnp,
-                                                    const float2* __restrict__ tw, float2* __restrict__ X, int p0,
-                                                    bool conj_out = false) {
+                                                    const float* __restrict__ a, const float2* __restrict__ tw,
+                                                    float2* __restrict__ X, int p0, bool conj_out = false) {
   using S = TileShape<NP>;
-  auto src = [&](int c, int n) -> float2 {
+  auto src = [&](int c, int j) -> float2 {
     const int p = p0 + c;
     if (p >= P) return make_float2(0.f, 0.f);
+    const int n = (j - (int)(((int64_t)p * L) & (NP - 1))) & (NP - 1);    // j = (pL + n) mod Np
     return cscale(__ldg(x + (int64_t)p * L + n), __ldg(a + n));
   };
   auto dst = [&](int c, int f, float2 v) {
     const int p = p0 + c;
     if (p >= P) return;
-    const int pl = (int)(((int64_t)p * L) & (NP - 1));          // (p L) mod Np
-    const int kh = (f + NP / 2) & (NP - 1);
-    float2 r = cmul(v, __ldg(wnp + ((f * pl) & (NP - 1))));
-    if (conj_out) r.y = -r.y;
-    X[(int64_t)kh * P + p] = r;
+    if (conj_out) v.y = -v.y;
+    X[(int64_t)((f + NP / 2) & (NP - 1)) * P + p] = v;
   };
   tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
@@ -77,33 +76,31 @@ __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const flo
 
 // ---------------------------------------------------------------- SSCA channeliser + CDP (K3)
 // time points n0 .. n0 + C - 1:  X_g[kh][n] = W_Np^{(k s) mod Np} DFT_Np(a x[s ..])[k] conj(y[n])
-// (y = x for the auto estimate; conj: y[n] itself, the conjugate estimate)
+// (y = x for the auto estimate; conj: y[n] itself, the conjugate estimate).  As in K1 the
+// down-conversion is the placement of a[r] x[s+r] at FFT input position (s + r) mod Np.
 template <int NP, bool TC>
 __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x,
                                               const float2* __restrict__ y, bool conj, int N,
-                                              const float* __restrict__ a, const float2* __restrict__ wnp,
-                                              const float2* __restrict__ tw, float2* __restrict__ Xg, int n0) {
+                                              const float* __restrict__ a, const float2* __restrict__ tw,
+                                              float2* __restrict__ Xg, int n0) {
   using S = TileShape<NP>;
   // this thread's time point (transforms interleaved: c = tid % C), resolved once
   const int n = n0 + (int)threadIdx.x % S::C;
   const bool interior = n0 - NP / 2 >= 0 && n0 + S::C + NP / 2 <= N;   // whole tile away from the ends
-  const float2* __restrict__ xb = x + (n - NP / 2);
-  float2 xn = __ldg(y + n);                                        // the factor is conj(xn)
+  const int s = n - NP / 2;                                         // window start (may be < 0)
+  const int smod = s & (NP - 1);
+  float2 xn = __ldg(y + n);                                         // the factor is conj(xn)
   if (conj) xn.y = -xn.y;
-  const int s = (n - NP / 2) & (NP - 1);                            // s mod Np (s may be < 0)
   float2* __restrict__ o = Xg + n;
-  auto src = [&](int, int r) -> float2 {
+  auto src = [&](int, int j) -> float2 {
+    const int r = (j - smod) & (NP - 1);                            // j = (s + r) mod Np
     if (!interior) {
-      const int m = n - NP / 2 + r;
+      const int m = s + r;
       if (m < 0 || m >= N) return make_float2(0.f, 0.f);
     }
-    return cscale(__ldg(xb + r), __ldg(a + r));
+    return cscale(__ldg(x + (s + r)), __ldg(a + r));
   };
-  auto dst = [&](int, int f, float2 v) {
-    const int kh = (f + NP / 2) & (NP - 1);
-    const float2 y = cmul(v, __ldg(wnp + ((f * s) & (NP - 1))));
-    o[(int64_t)kh * N] = cmulc(y, xn);
-  };
+  auto dst = [&](int, int f, float2 v) { o[(int64_t)((f + NP / 2) & (NP - 1)) * N] = cmulc(v, xn); };
   tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
 
