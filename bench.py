@@ -563,6 +563,41 @@ def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
     del Sf, Ss, work
     torch.cuda.empty_cache()
     out["sizes"] = "FAM N=65728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256; FP32 form; %d calls each" % reps
+    # streaming: one group of windows per step, new samples copied in from pinned host memory
+    # every step (scd_stream_advance) and the plan's graph replayed (scd_batch_run)
+    for name, est, W, hop, nwin, Npw, Lw in (("ssca_stream", "ssca", 1 << 16, 1 << 15, 16, 256, 1),
+                                              ("fam_stream", "fam", 65728, 16384, 8, 256, 64)):
+        plan = binding.StreamPlan(est, W, hop, nwin, Npw, Lw)
+        total = plan.span + (reps + warmup) * nwin * hop
+        sx = signals.modulated("qpsk", total, 4, 0.1, 10.0, seed=6300)
+        arena = torch.from_numpy(sx[:plan.span].copy()).to(dev)
+        # group k >= 1 takes the samples from k*nwin*hop + keep = span + (k-1)*nwin*hop on
+        chunks = [torch.from_numpy(sx[plan.span + g * nwin * hop:][:nwin * hop].copy()).pin_memory()
+                  for g in range(reps + warmup)]
+        sout = torch.empty(plan.out_offsets[-1], dtype=torch.complex64, device=dev)
+        sws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            plan.run(arena, sout, sws, stream=stream)
+            for g in range(warmup):
+                plan.advance(arena, chunks[g], stream=stream)
+                plan.run(arena, sout, sws, stream=stream)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for g in range(warmup, warmup + reps):
+                plan.advance(arena, chunks[g], stream=stream)
+                plan.run(arena, sout, sws, stream=stream)
+            t1.record(stream)
+            t1.synchronize()
+        binding.scd_check_device(stream)
+        ms = t0.elapsed_time(t1) / reps
+        nbytes = 8 * nwin * hop + (plan.out_offsets[-1]) * 8
+        out[name] = {"ms_per_group": round(ms, 5), "windows_per_group": nwin, "window": W, "hop": hop, "Np": Npw,
+                     "stream_msamples_per_s": round(nwin * hop / (ms * 1e-3) / 1e6, 2),
+                     "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "timed": "host-to-device copy of the group's new samples + the persistent launch"}
+        plan.close()
+        del arena, sout, sws
+        torch.cuda.empty_cache()
     return out
 
 

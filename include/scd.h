@@ -188,7 +188,9 @@ typedef struct scd_batch_plan scd_batch_plan;
 SCD_API scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np,
                                          int32_t L, int32_t precision, scd_batch_plan** out);
 /* Layout of the arenas (any output pointer may be NULL):
- *   x_offsets[nsig+1]    signal i is x_arena[x_offsets[i] .. x_offsets[i+1]) (its full length)
+ *   x_offsets[nsig+1]    signal i starts at x_arena[x_offsets[i]] (batches: it is
+ *                        x_arena[x_offsets[i] .. x_offsets[i+1]); streaming windows overlap);
+ *                        x_offsets[nsig] is the arena's length in samples
  *   out_offsets[nsig+1]  its estimate starts at out_arena + out_offsets[i] (complex64 elements):
  *                        FAM [Np][Np][P_i], SSCA [Np][N_i], as scd_fam / scd_ssca lay them out
  *   sizes[nsig]          P_i (FAM) or N_i (SSCA);  used_len[nsig]  samples consumed
@@ -204,6 +206,28 @@ SCD_API scd_status scd_batch_query(const scd_batch_plan* plan, int64_t* x_offset
 SCD_API scd_status scd_batch_run(scd_batch_plan* plan, const void* x_arena, const float* window, void* out_arena,
                                  void* workspace, void* stream);
 SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
+
+/* ------------------------------------------------------------------------------ streaming
+ * Successive windows of one continuous signal (the real-time use the paper targets, Sec. I):
+ * a plan over nwin windows of window_len samples, window i starting at sample i * hop of the
+ * x arena (x_offsets[i] = i * hop; the arena holds span = (nwin - 1) hop + window_len
+ * samples).  It is a batch plan in every other respect: scd_batch_query / run / tune /
+ * destroy apply, and the run replays one captured graph as long as the buffers and stream
+ * stay the same.  The windows' sizes follow the batch rules (FAM P from window_len and L,
+ * SSCA N = largest power of two <= window_len).  Needs nwin * hop >= window_len - hop.
+ *
+ * scd_stream_advance slides the arena to the next group of nwin windows: it moves the last
+ * keep = max(window_len - hop, 0) samples to the front (they belong to the next group's
+ * first windows) and copies span - keep samples from `samples` behind them; both copies are
+ * enqueued on `stream`.  `samples` (HOST memory if samples_on_host, else device memory)
+ * holds the nwin * hop stream samples that follow the kept ones: for group k >= 1 they
+ * start at stream sample k * nwin * hop + keep.  Start a stream by filling x_arena[0, span)
+ * with its first span samples.  After k advances the arena holds stream samples
+ * [k nwin hop, k nwin hop + span), so window i of group k is stream window k * nwin + i. */
+SCD_API scd_status scd_stream_plan_create(int32_t estimator, int64_t window_len, int64_t hop, int32_t nwin,
+                                          int32_t Np, int32_t L, int32_t precision, scd_batch_plan** out);
+SCD_API scd_status scd_stream_advance(scd_batch_plan* plan, void* x_arena, const void* samples,
+                                      int32_t samples_on_host, void* stream);
 
 /* ------------------------------------------------------------------------------ autotuner
  * The persistent schedule has two sizing knobs: how much output one queue item covers (the

@@ -59,6 +59,8 @@ SIGNATURES = {
     "scd_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "scd_batch_plan_destroy": (None, [_vp]),
     "scd_batch_tune": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
+    "scd_stream_plan_create": (_i32, [_i32, _i64, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_void_p)]),
+    "scd_stream_advance": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "scd_ssca_tune": (_i32, [_vp, _i64, _i32, _vp, _vp, _opts_p, _i32]),
     "scd_events_create": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_events_destroy": (_i32, [_i32, ctypes.POINTER(ctypes.c_void_p)]),
@@ -304,7 +306,10 @@ class BatchPlan:
         check(lib.scd_batch_plan_create({"fam": 0, "ssca": 1}[estimator], self.nsig, arr, Np, L, prec,
                                         ctypes.byref(handle)), "scd_batch_plan_create")
         self.handle = handle
-        n = self.nsig
+        self._query()
+
+    def _query(self):
+        lib, handle, n = self.lib, self.handle, self.nsig
         xo, oo = (ctypes.c_int64 * (n + 1))(), (ctypes.c_int64 * (n + 1))()
         sz, used = (ctypes.c_int64 * n)(), (ctypes.c_int64 * n)()
         ws = ctypes.c_size_t()
@@ -343,3 +348,38 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+class StreamPlan(BatchPlan):
+    """Successive windows of one continuous signal (scd_stream_plan_create / scd_stream_advance):
+    nwin windows of window_len samples every hop samples per group.  The arenas are torch
+    tensors as for BatchPlan; x_offsets[-1] is the arena length (span)."""
+
+    def __init__(self, estimator: str, window_len: int, hop: int, nwin: int, Np: int, L: int = 1,
+                 precision="fp32"):
+        lib = load()
+        self.lib = lib
+        self.estimator = estimator
+        self.nsig = nwin
+        self.Np, self.L = Np, L
+        self.window_len, self.hop = window_len, hop
+        handle = ctypes.c_void_p()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        check(lib.scd_stream_plan_create({"fam": 0, "ssca": 1}[estimator], window_len, hop, nwin, Np, L, prec,
+                                         ctypes.byref(handle)), "scd_stream_plan_create")
+        self.handle = handle
+        self._query()
+
+    @property
+    def span(self):
+        return self.x_offsets[-1]
+
+    def advance(self, x_arena, samples, stream=None):
+        """Slides x_arena to the next group; samples: the next nwin*hop stream samples, a
+        complex64 tensor on the host (pinned for full speed) or on the device."""
+        torch = _torch()
+        _need(x_arena, torch.complex64, self.span, "x_arena")
+        if samples.dtype != torch.complex64 or not samples.is_contiguous() or samples.numel() < self.nsig * self.hop:
+            raise TypeError(f"samples must be a contiguous complex64 tensor of {self.nsig * self.hop} elements")
+        check(self.lib.scd_stream_advance(self.handle, _ptr(x_arena), _ptr(samples), 0 if samples.is_cuda else 1,
+                                          _stream(stream)), "scd_stream_advance")

@@ -336,6 +336,8 @@ struct scd_batch_plan {
   const void* g_out = nullptr;
   const void* g_ws = nullptr;
   void* g_stream = nullptr;
+  // streaming plans (scd_stream_plan_create): window length and hop; 0 for batches
+  int64_t stream_window = 0, stream_hop = 0;
 };
 
 namespace {
@@ -518,12 +520,10 @@ scd_status time_candidate(cudaStream_t st, int reps, Run run, float* ms) {
   return s;
 }
 
-}  // namespace
-
-extern "C" {
-
-scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np, int32_t L,
-                                 int32_t precision, scd_batch_plan** out) {
+// Plan over nsig signals: signal i has lengths[i] samples starting at starts[i] of the x arena
+// (starts == nullptr: packed back to back); the arena holds `span` samples (0: the sum).
+scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, const int64_t* starts, int64_t span,
+                       int32_t Np, int32_t L, int32_t precision, scd_batch_plan** out) {
   using namespace scd;
   if (!out || !lengths || nsig < 1 || (estimator != 0 && estimator != 1)) return SCD_ERR_ARG;
   *out = nullptr;
@@ -553,7 +553,8 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     if (!sz) { free_plan(p); return SCD_ERR_ARG; }               // signal too short
     p->sizes[i] = sz;
     p->used[i] = used;
-    p->x_off[i + 1] = p->x_off[i] + len;
+    if (starts) p->x_off[i] = starts[i];
+    p->x_off[i + 1] = starts ? span : p->x_off[i] + len;
     const int64_t outn = fam ? (int64_t)Np * Np * sz : (int64_t)Np * sz;
     p->out_off[i + 1] = p->out_off[i] + outn;
     p->ws_off[i + 1] = p->ws_off[i] + (int64_t)Np * sz;
@@ -570,6 +571,7 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
     auto mix = [&](int64_t v) { for (int b = 0; b < 8; ++b) { h ^= (uint64_t)((v >> (8 * b)) & 0xFF); h *= 1099511628211ull; } };
     mix(estimator); mix(Np); mix(L); mix(precision); mix(nsig);
     for (int i = 0; i < nsig; ++i) mix(lengths[i]);
+    if (starts) { mix(span); for (int i = 0; i < nsig; ++i) mix(starts[i]); }
     p->signature = h;
     TuneEntry te;
     if (tune_lookup(batch_key(p), &te)) { p->item_bytes = te.item_bytes; p->slot_bytes = te.slot_bytes; }
@@ -590,6 +592,47 @@ scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t*
   p->grid = sms * (per_sm > 0 ? per_sm : 1);
   *out = p;
   return SCD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np, int32_t L,
+                                 int32_t precision, scd_batch_plan** out) {
+  return plan_create(estimator, nsig, lengths, nullptr, 0, Np, L, precision, out);
+}
+
+scd_status scd_stream_plan_create(int32_t estimator, int64_t window_len, int64_t hop, int32_t nwin, int32_t Np,
+                                  int32_t L, int32_t precision, scd_batch_plan** out) {
+  if (!out || window_len < 1 || hop < 1 || nwin < 1) return SCD_ERR_ARG;
+  // the overlap kept between groups must not overlap the part it is copied from
+  if (window_len > hop && (int64_t)nwin * hop < window_len - hop) return SCD_ERR_ARG;
+  std::vector<int64_t> lengths((size_t)nwin, window_len), starts((size_t)nwin);
+  for (int i = 0; i < nwin; ++i) starts[i] = (int64_t)i * hop;
+  const int64_t span = (int64_t)(nwin - 1) * hop + window_len;
+  scd_status s = plan_create(estimator, nwin, lengths.data(), starts.data(), span, Np, L, precision, out);
+  if (s == SCD_OK) {
+    (*out)->stream_window = window_len;
+    (*out)->stream_hop = hop;
+  }
+  return s;
+}
+
+scd_status scd_stream_advance(scd_batch_plan* p, void* x_arena, const void* samples, int32_t samples_on_host,
+                              void* stream) {
+  using namespace scd;
+  if (!p || !x_arena || !samples || !p->stream_hop || ((uintptr_t)x_arena % 8)) return SCD_ERR_ARG;
+  const int64_t W = p->stream_window, H = p->stream_hop, span = p->x_off[p->nsig];
+  const int64_t keep = W > H ? W - H : 0;                       // samples shared with the next group
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  float2* xa = (float2*)x_arena;
+  if (keep && (e = cudaMemcpyAsync(xa, xa + (span - keep), sizeof(float2) * (size_t)keep, cudaMemcpyDeviceToDevice,
+                                   st)) != cudaSuccess)
+    return cuda_status(e);
+  e = cudaMemcpyAsync(xa + keep, samples, sizeof(float2) * (size_t)(span - keep),
+                      samples_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
 }
 
 scd_status scd_batch_query(const scd_batch_plan* p, int64_t* x_offsets, int64_t* out_offsets, int64_t* sizes,

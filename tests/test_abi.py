@@ -149,3 +149,12 @@ def test_opts_layout_matches_header(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(binding.ScdOpts)] + [getattr(binding.ScdOpts, f).offset for f in fields]
     assert got == want
+
+
+def test_stream_plan_validation(lib):
+    h = ctypes.c_void_p()
+    assert lib.scd_stream_plan_create(1, 4096, 0, 4, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG   # hop 0
+    assert lib.scd_stream_plan_create(1, 4096, 1024, 0, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG  # no window
+    # the kept overlap (W - hop = 3072) would overlap its own source (nwin * hop = 2048)
+    assert lib.scd_stream_plan_create(1, 4096, 1024, 2, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
+    assert lib.scd_stream_advance(None, FAKE, FAKE, 0, None) == binding.SCD_ERR_ARG
