@@ -43,6 +43,8 @@ import numpy as np
 
 __all__ = [
     "hamming_window",
+    "chebyshev_window",
+    "chebyshev_window64",
     "twiddle",
     "fam_demodulates",
     "fam",
@@ -66,6 +68,37 @@ def hamming_window(Np: int) -> np.ndarray:
     float32 (the window bits both sides consume when the caller passes none)."""
     n = np.arange(Np, dtype=np.float64)
     return (0.54 - 0.46 * np.cos(2.0 * np.pi * n / (Np - 1))).astype(np.float32)
+
+
+def chebyshev_window64(Np: int, atten_db: float) -> np.ndarray:
+    """Dolph-Chebyshev window (Algorithms 1 and 2 window the channeliser input with
+    `chebwin[Np]`) in FP64: equiripple sidelobes atten_db below the main lobe.  From the
+    textbook definition: the window's Np-point spectrum samples are the Chebyshev polynomial
+    T_{Np-1}(x0 cos(pi k / Np)) with x0 = cosh(acosh(10^{atten/20}) / (Np - 1)); the window,
+    symmetric about (Np - 1)/2, is their inverse DFT (a real cosine sum), scaled to a peak of 1.
+    """
+    M = Np - 1
+    x0 = np.cosh(np.arccosh(10.0 ** (atten_db / 20.0)) / M)
+
+    def cheb(x):
+        x = np.asarray(x, dtype=np.float64)
+        inside = np.abs(x) <= 1.0
+        out = np.empty_like(x)
+        out[inside] = np.cos(M * np.arccos(x[inside]))
+        big = np.cosh(M * np.arccosh(np.abs(x[~inside])))
+        out[~inside] = np.where((x[~inside] < 0) & (M % 2 == 1), -big, big)
+        return out
+
+    k = np.arange(1, (Np - 1) // 2 + 1, dtype=np.float64)
+    Wk = cheb(x0 * np.cos(np.pi * k / Np))
+    n = np.arange(Np, dtype=np.float64)
+    w = cheb(np.array([x0]))[0] + 2.0 * (np.cos(2.0 * np.pi * np.outer(n - (Np - 1) / 2.0, k) / Np) @ Wk)
+    return w / np.max(w)
+
+
+def chebyshev_window(Np: int, atten_db: float = 100.0) -> np.ndarray:
+    """chebyshev_window64 rounded to float32 (the window bits both sides consume)."""
+    return chebyshev_window64(Np, atten_db).astype(np.float32)
 
 
 def twiddle(M: int, idx) -> np.ndarray:

@@ -1,0 +1,35 @@
+"""Pins of the Dolph-Chebyshev window (the `chebwin[Np]` of Algorithms 1 and 2) against
+scipy's chebwin, a library routine, and against the window's defining properties."""
+import numpy as np
+import pytest
+
+from oracle import scd_oracle as orc
+
+
+@pytest.mark.parametrize("Np", [16, 31, 32, 64, 100, 128, 256])
+@pytest.mark.parametrize("atten", [50.0, 80.0, 100.0])
+def test_chebyshev_matches_scipy(Np, atten):
+    windows = pytest.importorskip("scipy.signal.windows")
+    ref = windows.chebwin(Np, at=atten, sym=True)
+    got = orc.chebyshev_window64(Np, atten)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("Np,atten", [(64, 60.0), (256, 100.0)])
+def test_chebyshev_equiripple_sidelobes(Np, atten):
+    """Every sidelobe of the window's spectrum lies atten dB below the main lobe (equiripple:
+    the largest sidelobe equals the bound to a part in 10^6) and the window is symmetric."""
+    w = orc.chebyshev_window64(Np, atten)
+    assert np.allclose(w, w[::-1], rtol=0, atol=1e-14)
+    spec = np.abs(np.fft.fft(w, 64 * Np))
+    spec /= spec[0]
+    x0 = np.cosh(np.arccosh(10 ** (atten / 20)) / (Np - 1))
+    edge = np.arccos(1 / x0) / np.pi          # main-lobe half width in cycles/sample (cos(pi f) x0 = 1)
+    f = np.arange(spec.shape[0]) / spec.shape[0]
+    side = spec[(f > edge * 1.0001) & (f < 1 - edge * 1.0001)]
+    assert abs(20 * np.log10(side.max()) + atten) < 1e-4
+
+
+def test_chebyshev_float32_bits():
+    w = orc.chebyshev_window(64, 100.0)
+    assert w.dtype == np.float32 and w.max() == np.float32(1.0)
