@@ -301,6 +301,19 @@ SCD_API scd_status scd_check_device(void* stream);
 /* Number of kernels this library has launched in this process (all devices). */
 SCD_API uint64_t scd_launch_count(void);
 
+/* ------------------------------------------------------------------------------ windows
+ * scd_chebyshev_window: the Dolph-Chebyshev window that Algorithms 1 and 2 apply to the
+ * channeliser input (`chebwin[Np]`), for passing as `window` to the estimators: sidelobes
+ * atten_db below the main lobe (the paper gives no value; 100 dB is the customary default),
+ * symmetric about (Np - 1)/2, peak 1.  Computed on the device in FP64 from the definition
+ * (spectrum samples T_{Np-1}(x0 cos(pi k/Np)), x0 = cosh(acosh(10^{atten/20})/(Np-1)),
+ * inverted by a cosine sum) and rounded to float32 once.
+ *   Np      2 .. 256;  atten_db in (0, 300]
+ *   window  float32[Np] device pointer (4-byte aligned), fully overwritten
+ *   stream  cudaStream_t to enqueue on
+ * Errors: SCD_ERR_ARG (NULL/misaligned window, Np or atten_db out of range), SCD_ERR_CUDA. */
+SCD_API scd_status scd_chebyshev_window(int32_t Np, double atten_db, float* window, void* stream);
+
 /* ------------------------------------------------------------------------------ misc */
 /* Builds the cached tables the given sizes need (estimator 0 = FAM with (Np, P), 1 =
  * SSCA with (Np, N)), so that later calls may be captured in a CUDA graph. */

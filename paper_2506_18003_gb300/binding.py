@@ -69,6 +69,7 @@ SIGNATURES = {
     "scd_check_device": (_i32, [_vp]),
     "scd_launch_count": (ctypes.c_uint64, []),
     "scd_prepare": (_i32, [_i32, _i64, _i32, _i32]),
+    "scd_chebyshev_window": (_i32, [_i32, ctypes.c_double, _vp, _vp]),
     "scd_release_cache": (None, []),
     "scd_status_string": (ctypes.c_char_p, [_i32]),
     "scd_last_error": (ctypes.c_char_p, []),
@@ -276,6 +277,17 @@ def scd_ssca_tune(x, Np: int, window=None, out=None, precision="fp32", stream=No
     o = make_opts(stream, prec, ws)
     check(lib.scd_ssca_tune(_ptr(x), N, Np, _ptr(window), _ptr(out), ctypes.byref(o), reps), "scd_ssca_tune")
     return out
+
+
+def scd_chebyshev_window(Np: int, atten_db: float = 100.0, window=None, stream=None, device="cuda"):
+    """Dolph-Chebyshev window float32[Np] on the device (the chebwin of Algorithms 1 and 2)."""
+    torch = _torch()
+    lib = load()
+    if window is None:
+        window = torch.empty(Np, dtype=torch.float32, device=device)
+    _need(window, torch.float32, Np, "window")
+    check(lib.scd_chebyshev_window(Np, float(atten_db), _ptr(window), _stream(stream)), "scd_chebyshev_window")
+    return window
 
 
 def scd_check_device(stream=None) -> None:

@@ -243,6 +243,14 @@ scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const 
   return run_one(o, [&](cudaStream_t st) { return scd::ssca_map((const float2*)S, N, Np, o.map_power, map, st); });
 }
 
+scd_status scd_chebyshev_window(int32_t Np, double atten_db, float* window, void* stream) {
+  if (!window || !aligned(window, 4) || Np < 2 || Np > 256) return SCD_ERR_ARG;
+  if (!(atten_db > 0.0 && atten_db <= 300.0)) return SCD_ERR_ARG;   // also rejects NaN
+  scd::count_launches(1);
+  cudaError_t e = scd::build_chebyshev_into(window, Np, atten_db, (cudaStream_t)stream);
+  return e == cudaSuccess ? SCD_OK : cuda_fail(e);
+}
+
 scd_status scd_prepare(int32_t estimator, int64_t N, int32_t Np, int32_t P) {
   if (!np_ok(Np)) return SCD_ERR_UNSUPPORTED;
   cudaError_t e;

@@ -28,6 +28,7 @@ void release_tables();
 // synchronisation; enqueued on st).
 cudaError_t build_pass_into(float2* out, int M, cudaStream_t st);   // PlanInfo<M>::tw_len() entries
 cudaError_t build_hamming_into(float* out, int Np, cudaStream_t st);
+cudaError_t build_chebyshev_into(float* out, int Np, double atten_db, cudaStream_t st);   // Np <= 256
 
 // ---------------------------------------------------------------- FAM (fam.cu)
 // X[kh][p] = W_Np^{(k p L) mod Np} sum_n a[n] x[pL + n] W_Np^{(k n) mod Np}  (conj(X) if conj_out)

@@ -1,9 +1,9 @@
 // K0: FP64 phase and twiddle tables.
 //
-// The down-conversion phases W_Np^{(k p L) mod Np} (Eq. II.B-complex_demodulate_final),
-// W_Np^{(k s) mod Np} (SSCA channeliser), the rotate factor W_N^{(m2 m1') mod N} of the
-// decomposed FFT (Eq. Chap4_2DFFT) and the Stockham pass twiddles are all of the form
-// W_M^j with an exact integer j in [0, M).  Each entry is computed once with FP64
+// The rotate factor W_N^{(m2 m1') mod N} of the decomposed FFT (Eq. Chap4_2DFFT) and the
+// Stockham pass twiddles are all of the form W_M^j with an exact integer j in [0, M) (the
+// channelisers' down-conversion phases need no table: they are folded into the FFT's input
+// order).  Each entry is computed once with FP64
 // sincospi(2 j / M) (argument exact: M is a power of two) and rounded to float32, so no
 // phase ever loses accuracy to an FP32 angle, even at M = 2^20.
 #include <map>
@@ -72,6 +72,36 @@ __global__ void k_dftmat(unsigned char* out, int R, int Kp) {
 __global__ void k_hamming(float* out, int Np) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < Np) out[n] = (float)(0.54 - 0.46 * cospi(2.0 * (double)n / (double)(Np - 1)));
+}
+
+// Dolph-Chebyshev window (the `chebwin` of Algorithms 1 and 2), one block of Np <= 256
+// threads, FP64 throughout: spectrum samples W(k) = T_{Np-1}(x0 cos(pi k / Np)) with
+// x0 = cosh(acosh(10^{A/20}) / (Np - 1)); the window symmetric about (Np - 1)/2 is the real
+// cosine sum w[n] = W(0) + 2 sum_{k=1}^{floor((Np-1)/2)} W(k) cos(pi k (2n - Np + 1) / Np),
+// scaled to a peak of 1 and rounded to float32 once.
+__device__ double chebyshev_poly(int M, double x) {
+  if (fabs(x) <= 1.0) return cos(M * acos(x));
+  const double v = cosh(M * acosh(fabs(x)));
+  return (x < 0.0 && (M & 1)) ? -v : v;
+}
+
+__global__ void __launch_bounds__(256) k_chebwin(float* out, int Np, double atten_db) {
+  __shared__ double red[256];
+  const int n = threadIdx.x, M = Np - 1;
+  const double x0 = cosh(acosh(pow(10.0, atten_db / 20.0)) / M);
+  double v = 0.0;
+  if (n < Np) {
+    v = chebyshev_poly(M, x0);
+    for (int k = 1; k <= (Np - 1) / 2; ++k)
+      v += 2.0 * chebyshev_poly(M, x0 * cospi((double)k / Np)) * cospi((double)(k * (2 * n - Np + 1)) / Np);
+  }
+  red[n] = n < Np ? v : -1.0e300;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (n < s) red[n] = fmax(red[n], red[n + s]);
+    __syncthreads();
+  }
+  if (n < Np) out[n] = (float)(v / red[0]);
 }
 
 struct Key {
@@ -160,6 +190,11 @@ cudaError_t build_pass_into(float2* out, int M, cudaStream_t st) {
   if (!r.r1) return cudaSuccess;                               // single-pass plans use no table
   const int len = r.r0 * r.r1 + (r.r2 ? r.r0 * r.r1 * r.r2 : 0);
   k_pass<<<grid_for(len), 256, 0, st>>>(out, M, r.r0, r.r1, r.r2);
+  return cudaGetLastError();
+}
+
+cudaError_t build_chebyshev_into(float* out, int Np, double atten_db, cudaStream_t st) {
+  k_chebwin<<<1, 256, 0, st>>>(out, Np, atten_db);
   return cudaGetLastError();
 }
 

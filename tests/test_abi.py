@@ -158,3 +158,11 @@ def test_stream_plan_validation(lib):
     # the kept overlap (W - hop = 3072) would overlap its own source (nwin * hop = 2048)
     assert lib.scd_stream_plan_create(1, 4096, 1024, 2, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
     assert lib.scd_stream_advance(None, FAKE, FAKE, 0, None) == binding.SCD_ERR_ARG
+
+
+def test_chebyshev_window_validation(lib):
+    assert lib.scd_chebyshev_window(1, 100.0, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_chebyshev_window(257, 100.0, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_chebyshev_window(64, 0.0, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_chebyshev_window(64, float("nan"), FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_chebyshev_window(64, 100.0, None, None) == binding.SCD_ERR_ARG
