@@ -267,6 +267,42 @@ class BatchWorkload:
     def stage_times(self, marks):
         return {"fam_batch": marks[0].elapsed_time(marks[1]), "ssca_batch": marks[1].elapsed_time(marks[2])}
 
+    def profile_mode(self, torch, binding, stream, reps=10, warmup=3):
+        """The same step with the plans' alpha-profile output (the estimates are reduced to one
+        float per alpha column inside the kernels and never written): FP32 form, CUDA events
+        around `reps` steps after `warmup`."""
+        dev = self.x.device
+        plans = []
+        for est, Np, L in (("fam", self.FAM_NP, self.FAM_L), ("ssca", self.SSCA_NP, 1)):
+            pl = binding.BatchPlan(est, self.lengths, Np, L, "fp32")
+            pl.set_output("profile", 1)
+            plans.append((pl, torch.empty(pl.out_offsets[-1], dtype=torch.float32, device=dev)))
+        with torch.cuda.stream(stream):
+            for pl, out in plans:
+                pl.tune(self.x, out, self.ws, stream=stream, reps=2)
+            for _ in range(warmup):
+                for pl, out in plans:
+                    pl.run(self.x, out, self.ws, stream=stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            tf = ts = 0.0
+            for _ in range(reps):
+                ev[0].record(stream)
+                plans[0][0].run(self.x, plans[0][1], self.ws, stream=stream)
+                ev[1].record(stream)
+                plans[1][0].run(self.x, plans[1][1], self.ws, stream=stream)
+                ev[2].record(stream)
+                ev[2].synchronize()
+                tf += ev[0].elapsed_time(ev[1]) / reps
+                ts += ev[1].elapsed_time(ev[2]) / reps
+        binding.scd_check_device(stream)
+        out_bytes = 4 * (plans[0][0].out_offsets[-1] + plans[1][0].out_offsets[-1])
+        for pl, _ in plans:
+            pl.close()
+        return {"ms_per_step": round(tf + ts, 4), "stage_ms": {"fam_batch": round(tf, 4), "ssca_batch": round(ts, 4)},
+                "msamples_per_s": round(self.samples_per_step() / ((tf + ts) * 1e-3) / 1e6, 2),
+                "output_bytes_per_step": out_bytes,
+                "note": "alpha profiles (|S| max over f per alpha) fused into the last stage; FP32 form; tuned"}
+
     def e2e(self, prec, stream, steps, world, torch):
         """H2D of the input arena from pinned memory, both batched estimates, D2H of both
         output arenas into pinned memory, every step (public Python binding)."""
@@ -712,6 +748,8 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             line["e2e"] = wl.e2e(prec, stream, min(args.steps, args.e2e_steps), world, torch)
     if not args.no_variants:
+        if hasattr(wl, "profile_mode"):
+            line["profile_output"] = wl.profile_mode(torch, binding, stream)
         line["variants"] = measure_variants(torch, binding, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, desc = wl.oracle_sample()

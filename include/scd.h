@@ -206,6 +206,14 @@ SCD_API scd_status scd_batch_query(const scd_batch_plan* plan, int64_t* x_offset
 SCD_API scd_status scd_batch_run(scd_batch_plan* plan, const void* x_arena, const float* window, void* out_arena,
                                  void* workspace, void* stream);
 SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
+/* Output of the plan's runs: mode 0 = the estimates (default); 1 / 2 = only each signal's
+ * alpha profile of |S| / |S|^2 (scd_fam_alpha_profile / scd_ssca_alpha_profile of its
+ * estimate, bit for bit), reduced inside the last stage so the estimate is never written
+ * (the output shrinks from Np^2 P_i or Np N_i complex values to 2 P_i L or 2 N_i floats).
+ * Changes the layout: scd_batch_query then gives out_offsets in float32 elements and the
+ * out arena is float32[out_offsets[nsig]], zeroed by every run.  FAM needs 2 L <= Np and
+ * P_i L divisible by Np for every signal (else SCD_ERR_UNSUPPORTED). */
+SCD_API scd_status scd_batch_plan_set_output(scd_batch_plan* plan, int32_t mode);
 
 /* ------------------------------------------------------------------------------ streaming
  * Successive windows of one continuous signal (the real-time use the paper targets, Sec. I):

@@ -58,6 +58,7 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_size_t)]),
     "scd_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "scd_batch_plan_destroy": (None, [_vp]),
+    "scd_batch_plan_set_output": (_i32, [_vp, _i32]),
     "scd_batch_tune": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "scd_stream_plan_create": (_i32, [_i32, _i64, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_stream_advance": (_i32, [_vp, _vp, _vp, _i32, _vp]),
@@ -320,6 +321,19 @@ class BatchPlan:
         self.handle = handle
         self._query()
 
+    profile_power = 0
+
+    def set_output(self, mode: str = "estimate", power: int = 1):
+        """mode "estimate" (the SCD of every signal) or "profile" (only each signal's alpha
+        profile of |S|^power, reduced inside the kernel; the out arena becomes float32)."""
+        p = 0 if mode == "estimate" else int(power)
+        check(self.lib.scd_batch_plan_set_output(self.handle, p), "scd_batch_plan_set_output")
+        self.profile_power = p
+        self._query()
+
+    def out_dtype(self):
+        return _torch().float32 if self.profile_power else _torch().complex64
+
     def _query(self):
         lib, handle, n = self.lib, self.handle, self.nsig
         xo, oo = (ctypes.c_int64 * (n + 1))(), (ctypes.c_int64 * (n + 1))()
@@ -333,7 +347,7 @@ class BatchPlan:
     def run(self, x_arena, out_arena, workspace, window=None, stream=None):
         torch = _torch()
         _need(x_arena, torch.complex64, self.x_offsets[-1], "x_arena")
-        _need(out_arena, torch.complex64, self.out_offsets[-1], "out_arena")
+        _need(out_arena, self.out_dtype(), self.out_offsets[-1], "out_arena")
         check(self.lib.scd_batch_run(self.handle, _ptr(x_arena), _ptr(window), _ptr(out_arena),
                                      _ptr(workspace), _stream(stream)), "scd_batch_run")
 
@@ -346,6 +360,8 @@ class BatchPlan:
     def output(self, out_arena, i):
         """View of signal i's estimate in the output arena."""
         a, b = self.out_offsets[i], self.out_offsets[i + 1]
+        if self.profile_power:
+            return out_arena[a:b]
         if self.estimator == "fam":
             return out_arena[a:b].view(self.Np, self.Np, self.sizes[i])
         return out_arena[a:b].view(self.Np, self.sizes[i])

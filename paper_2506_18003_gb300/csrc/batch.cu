@@ -23,278 +23,46 @@
 #include <tuple>
 #include <vector>
 
-#include "internal.h"
-#include "tiles.cuh"
+#include "batch_kernel.cuh"
 
 namespace scd {
-namespace {
-
-enum Op : int32_t { OP_FAM_CHAN = 0, OP_FAM_PAIRS = 1, OP_SSCA_CDP = 2, OP_SSCA_COLS = 3, OP_SSCA_ROWS = 4 };
-
-struct Task {
-  int32_t op, size, dep, bbytes;          // op, transform size, prerequisite task (-1), B bytes
-  int32_t dep2, ch0;                      // second prerequisite (-1); SSCA: first channel of the unit
-  int64_t first, tiles;                   // queue items [first, first + tiles)
-  int64_t subtiles;                       // CTA tiles of the task; one queue item covers `per_item`
-  int32_t per_item, pad_;
-  int64_t x_off, out_off, ws_off;         // element offsets into the arenas
-  int64_t mid_off;                        // SSCA: workspace offset of the unit's column-pass slot
-  int32_t N, P, M1, M2;                   // the signal's sizes
-  const float2* tw;                       // pass twiddles of this task's transform size
-  const float2* wN;                       // SSCA column pass: W_N^j
-  const float2* cols;                     // SSCA column pass: W_N^{c m1'} at [m1'][c]
-  const unsigned char* bmats;             // split form: B matrices of this size
-};
-
-struct BatchArgs {
-  const Task* tasks;
-  int32_t ntasks, Np, L;
-  int64_t total;                          // tiles in the whole plan
-  unsigned* counters;                     // [0]: next tile, [1 + t]: tiles of task t done
-  const float2* x;                        // x arena
-  const float2* y;                        // SSCA: second factor's arena (x for the auto estimate)
-  int32_t conj, pad_;                     // SSCA: 1 = conjugate estimate (y unconjugated)
-  float2* out;                            // output arena
-  float2* ws;                             // workspace arena
-  const float* window;
-  const float2* tw_np;                    // pass twiddles of size Np
-  const unsigned char* bmats_np;          // split form: B matrices of size Np
-  int32_t bbytes_np;
-  unsigned* err;
-};
-
-constexpr int kThreads = 256;
-constexpr int kSlots = 3;                                  // rotating column-pass slots (SSCA)
-constexpr int64_t kSlotBytes = 16ll << 20;                 // target bytes of one slot
-constexpr int64_t kItemBytes = 128ll << 10;                // output bytes per queue item (target)
-constexpr int64_t kSlotBytesMax = 64ll << 20;              // largest slot the autotuner tries
-
-// Channels per SSCA unit: the largest power of two G <= Np with G N 8 <= slot bytes.
-int64_t slot_group(int Np, int64_t N, int64_t slot_bytes) {
-  int64_t G = Np;
-  while (G > 1 && G * N * 8 > slot_bytes) G >>= 1;
-  return G;
-}
-constexpr unsigned long long kWaitNs = 2000000000ull;   // bound on any dependency wait
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Shared-memory layout of the batch kernel: region 0 (largest over every size the estimator
-// may meet), then (split form) the largest B-matrix set, the tensor-core slot and slack.
-template <bool FAM, bool TC>
-struct BatchSmem {
-  template <int M, int EXTRA = 0>
-  using FS = FftSmem<M, TileShape<M>::C, TileShape<M>::NT, TC, EXTRA>;
-  static constexpr int mx(int a, int b) { return a > b ? a : b; }
-  static constexpr int fam_r0() {
-    return mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
-              mx(mx(FS<256>::region0, FS<512>::region0),
-                 mx(mx(FS<1024>::region0, FS<2048>::region0), mx(FS<4096>::region0, FS<8192>::region0))));
-  }
-  static constexpr int fam_b() {
-    return mx(mx(mx(FS<16>::bbytes, FS<32>::bbytes), mx(FS<64>::bbytes, FS<128>::bbytes)),
-              mx(mx(FS<256>::bbytes, FS<512>::bbytes),
-                 mx(mx(FS<1024>::bbytes, FS<2048>::bbytes), mx(FS<4096>::bbytes, FS<8192>::bbytes))));
-  }
-  static constexpr int ssca_r0() {
-    return mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
-              mx(mx(FS<256>::region0, FS<512>::region0),
-                 mx(mx(FS<1024>::region0, FS<64, rows_stage_bytes<64>()>::region0),
-                    mx(mx(FS<128, rows_stage_bytes<128>()>::region0, FS<256, rows_stage_bytes<256>()>::region0),
-                       mx(FS<512, rows_stage_bytes<512>()>::region0, FS<1024, rows_stage_bytes<1024>()>::region0)))));
-  }
-  static constexpr int ssca_b() {
-    return mx(mx(mx(FS<16>::bbytes, FS<32>::bbytes), mx(FS<64>::bbytes, FS<128>::bbytes)),
-              mx(mx(FS<256>::bbytes, FS<512>::bbytes), FS<1024>::bbytes));
-  }
-  static constexpr int region0 = FAM ? fam_r0() : ssca_r0();
-  static constexpr int bbytes = TC ? (FAM ? fam_b() : ssca_b()) : 0;
-  static constexpr int total = TC ? region0 + bbytes + 16 + 4096 : region0;
-  // TMEM columns: 256 threads, at most 32 values per thread, 2 fp32 columns per value
-  static constexpr int tmem_cols = 128;
-};
-
-template <bool TC>
-__device__ __forceinline__ void load_b(TcCtx& ctx, unsigned char* bsm, const unsigned char* bm, int bytes,
-                                       const unsigned char*& loaded) {
-  if constexpr (TC) {
-    if (loaded != bm) {
-      tc_load_b(ctx, bsm, bm, bytes);
-      loaded = bm;
-    }
-  }
-}
-
-template <bool TC>
-__device__ __forceinline__ void fam_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
-                         const unsigned char*& loaded) {
-  const float2* x = A.x + t.x_off;
-  float2* X = A.ws + t.ws_off;
-  if (t.op == OP_FAM_CHAN) {
-    load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
-    switch (A.Np) {
-#define SCD_CH(NPV) case NPV: fam_channelise_tile<NPV, TC>(sm, ctx, x, A.L, t.P, A.window, A.tw_np, X, (int)tile * TileShape<NPV>::C); break;
-      SCD_CH(16) SCD_CH(32) SCD_CH(64) SCD_CH(128) SCD_CH(256)
-#undef SCD_CH
-    }
-  } else {
-    load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
-    float2* out = A.out + t.out_off;
-    switch (t.P) {
-#define SCD_PR(PV) case PV: fam_pairs_tile<PV, TC>(sm, ctx, X, X, A.Np, out, t.tw, tile * TileShape<PV>::C); break;
-      SCD_PR(2) SCD_PR(4) SCD_PR(8) SCD_PR(16) SCD_PR(32) SCD_PR(64) SCD_PR(128) SCD_PR(256) SCD_PR(512)
-      SCD_PR(1024) SCD_PR(2048) SCD_PR(4096) SCD_PR(8192)
-#undef SCD_PR
-    }
-  }
-}
-
-template <bool TC>
-__device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int64_t tile, float2* sm, TcCtx& ctx, unsigned char* bsm,
-                          const unsigned char*& loaded) {
-  const float2* x = A.x + t.x_off;
-  float2* ws = A.ws + t.ws_off;
-  if (t.op == OP_SSCA_CDP) {
-    load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
-    switch (A.Np) {
-#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, A.y + t.x_off, A.conj != 0, t.N, A.window, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
-      SCD_CD(16) SCD_CD(32) SCD_CD(64) SCD_CD(128) SCD_CD(256)
-#undef SCD_CD
-    }
-  } else if (t.op == OP_SSCA_COLS) {
-    // unit of channels [ch0, ch0 + G): X_g rows of the signal -> the unit's slot
-    load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
-    switch (t.M1) {
-#define SCD_CO(MV)                                                                          \
-  case MV: {                                                                                \
-    constexpr int C = TileShape<MV>::C;                                                     \
-    const int per = t.M2 / C;                                                               \
-    const int64_t kh = tile / per;                                                          \
-    ssca_cols_tile<MV, TC, true>(sm, ctx, ws + (t.ch0 + kh) * t.N, A.ws + t.mid_off + kh * t.N, t.N, t.M2, t.wN, \
-                           t.cols, t.tw, (int)(tile % per) * C);                            \
-  } break;
-      SCD_CO(64) SCD_CO(128) SCD_CO(256) SCD_CO(512) SCD_CO(1024)
-#undef SCD_CO
-    }
-  } else {
-    load_b<TC>(ctx, bsm, t.bmats, t.bbytes, loaded);
-    float2* out = A.out + t.out_off;
-    switch (t.M2) {
-#define SCD_RO(MV)                                                                          \
-  case MV: {                                                                                \
-    constexpr int C = TileShape<MV>::C;                                                     \
-    const int per = t.M1 / C;                                                               \
-    const int64_t kh = tile / per;                                                          \
-    ssca_rows_tile<MV, TC, true>(sm, ctx, A.ws + t.mid_off + kh * t.N, out + (t.ch0 + kh) * t.N, t.M1, t.tw, \
-                           (int)(tile % per) * C);                                          \
-  } break;
-      SCD_RO(64) SCD_RO(128) SCD_RO(256) SCD_RO(512) SCD_RO(1024)
-#undef SCD_RO
-    }
-  }
-}
-
-template <bool FAM, bool TC>
-__global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs A) {
-  extern __shared__ __align__(128) float2 sm[];
-  __shared__ int64_t s_tile;
-  __shared__ int s_task;
-  __shared__ int s_skip;
-  using BS = BatchSmem<FAM, TC>;
-  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
-  TcCtx ctx{};
-  unsigned char* bsm = base + BS::region0;
-  if constexpr (TC) ctx = tc_open<BS::tmem_cols>(base + BS::region0 + BS::bbytes, A.err);
-  const unsigned char* loaded = nullptr;
-  // Scheduling state, kept by thread 0: the next tile index is claimed one tile ahead so the
-  // atomic's latency overlaps the current tile; a CTA's tiles only increase, so the task is
-  // found by scanning forward; a satisfied dependency is remembered per task.
-  int64_t next = 0;
-  int cur = 0, dep_ok_task = -1;
-  if (threadIdx.x == 0) next = (int64_t)atomicAdd(A.counters, 1u);
-  for (;;) {
-    __syncthreads();                                         // previous tile fully done with smem
-    if (threadIdx.x == 0) {
-      const int64_t tile = next;
-      s_tile = tile;
-      int skip = 0;
-      if (tile < A.total) {
-        next = (int64_t)atomicAdd(A.counters, 1u);           // claim the following tile now
-        while (cur + 1 < A.ntasks && __ldg(&A.tasks[cur + 1].first) <= tile) ++cur;
-        if (dep_ok_task != cur) {
-          const int deps[2] = {__ldg(&A.tasks[cur].dep), __ldg(&A.tasks[cur].dep2)};
-          const unsigned long long t0 = globaltimer();
-          for (int d = 0; d < 2 && !skip; ++d) {
-            if (deps[d] < 0) continue;
-            const unsigned need = (unsigned)__ldg(&A.tasks[deps[d]].tiles);
-            while (ld_acquire(A.counters + 1 + deps[d]) < need) {
-              if (globaltimer() - t0 > kWaitNs) {
-                atomicOr(A.err, 2u);
-                skip = 1;
-                break;
-              }
-              __nanosleep(128);
-            }
-          }
-          if (!skip) dep_ok_task = cur;
-        }
-      }
-      s_task = cur;
-      s_skip = skip;
-    }
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= A.total) break;
-    const Task& t = A.tasks[s_task];
-    if (!s_skip) {
-      const int64_t s0 = (tile - t.first) * t.per_item;
-      const int64_t s1 = s0 + t.per_item < t.subtiles ? s0 + t.per_item : t.subtiles;
-      for (int64_t st = s0; st < s1; ++st) {
-        if (st > s0) __syncthreads();                        // shared memory reused by the next tile
-        if constexpr (FAM) fam_tile<TC>(A, t, st, sm, ctx, bsm, loaded);
-        else ssca_tile<TC>(A, t, st, sm, ctx, bsm, loaded);
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(A.counters + 1 + s_task, 1u);
-    }
-  }
-  if constexpr (TC) tc_end<BS::tmem_cols>(ctx);
-}
-
+namespace bk {
 int smem_of(bool fam, bool tc) {
   if (fam) return tc ? BatchSmem<true, true>::total : BatchSmem<true, false>::total;
   return tc ? BatchSmem<false, true>::total : BatchSmem<false, false>::total;
 }
 
+namespace {
 template <bool FAM, bool TC>
-cudaError_t prepare_kernel(int smem, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch<FAM, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t prepare_one(int smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch<FAM, TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<FAM, TC>, kThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<FAM, TC, false>, kThreads, smem);
+}
+}  // namespace
+
+cudaError_t prepare_kernel(bool fam, bool tc, bool prof, int smem, int* blocks_per_sm) {
+  if (prof) return prepare_kernel_profile(fam, tc, smem, blocks_per_sm);
+  if (fam) return tc ? prepare_one<true, true>(smem, blocks_per_sm) : prepare_one<true, false>(smem, blocks_per_sm);
+  return tc ? prepare_one<false, true>(smem, blocks_per_sm) : prepare_one<false, false>(smem, blocks_per_sm);
 }
 
-cudaError_t launch_batch(bool fam, bool tc, int grid, int smem, const BatchArgs& A, cudaStream_t st) {
+cudaError_t launch_batch(bool fam, bool tc, bool prof, int grid, int smem, const BatchArgs& A, cudaStream_t st) {
+  if (prof) return launch_batch_profile(fam, tc, grid, smem, A, st);
   if (fam) {
-    if (tc) k_batch<true, true><<<grid, kThreads, smem, st>>>(A);
-    else k_batch<true, false><<<grid, kThreads, smem, st>>>(A);
+    if (tc) k_batch<true, true, false><<<grid, kThreads, smem, st>>>(A);
+    else k_batch<true, false, false><<<grid, kThreads, smem, st>>>(A);
   } else {
-    if (tc) k_batch<false, true><<<grid, kThreads, smem, st>>>(A);
-    else k_batch<false, false><<<grid, kThreads, smem, st>>>(A);
+    if (tc) k_batch<false, true, false><<<grid, kThreads, smem, st>>>(A);
+    else k_batch<false, false, false><<<grid, kThreads, smem, st>>>(A);
   }
   return cudaGetLastError();
 }
+}  // namespace bk
+
+using namespace bk;
+
+namespace {
 
 int tile_c(int M) {                       // transforms per tile for size M (256 threads)
   switch (M) {
@@ -314,12 +82,12 @@ int tile_c(int M) {                       // transforms per tile for size M (256
 
 struct scd_batch_plan {
   int estimator = 0, nsig = 0, Np = 0, L = 0, precision = 0, device = 0;
-  int64_t item_bytes = scd::kItemBytes;   // tunables (autotuner): output bytes per queue item,
-  int64_t slot_bytes = scd::kSlotBytes;   // bytes of one SSCA column-pass slot
+  int64_t item_bytes = scd::bk::kItemBytes;   // tunables (autotuner): output bytes per queue item,
+  int64_t slot_bytes = scd::bk::kSlotBytes;   // bytes of one SSCA column-pass slot
   uint64_t signature = 0;                 // hash of (estimator, Np, L, precision, lengths)
   std::vector<int64_t> x_off, out_off, ws_off, sizes, used;
-  std::vector<scd::Task> tasks;
-  scd::Task* d_tasks = nullptr;
+  std::vector<scd::bk::Task> tasks;
+  scd::bk::Task* d_tasks = nullptr;
   unsigned* d_counters = nullptr;
   int64_t total = 0;
   size_t ws_bytes = 0;
@@ -338,6 +106,9 @@ struct scd_batch_plan {
   void* g_stream = nullptr;
   // streaming plans (scd_stream_plan_create): window length and hop; 0 for batches
   int64_t stream_window = 0, stream_hop = 0;
+  // output mode (scd_batch_plan_set_output): 0 full estimates, 1 / 2 alpha profiles of |S|^1 / |S|^2
+  int prof_power = 0;
+  int grid_prof = 0;                      // grid of the profile kernel (0: not prepared yet)
 };
 
 namespace {
@@ -355,6 +126,18 @@ scd_status cuda_status(cudaError_t e) {
   snprintf(msg, sizeof msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   scd::set_last_error(msg);
   return SCD_ERR_CUDA;
+}
+
+// Output arena layout of the plan's mode: full estimates (complex64 elements: FAM Np^2 P_i,
+// SSCA Np N_i per signal) or alpha profiles (float32 elements: FAM 2 P_i L, SSCA 2 N_i).
+void layout_outputs(scd_batch_plan* p) {
+  const bool fam = p->estimator == 0;
+  const int64_t Np = p->Np;
+  for (int i = 0; i < p->nsig; ++i) {
+    const int64_t sz = p->sizes[i];
+    const int64_t n = p->prof_power ? (fam ? 2 * sz * p->L : 2 * sz) : (fam ? Np * Np * sz : Np * sz);
+    p->out_off[i + 1] = p->out_off[i] + n;
+  }
 }
 
 // (Re)builds the plan's task list with its current tunables and uploads it.
@@ -555,10 +338,9 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
     p->used[i] = used;
     if (starts) p->x_off[i] = starts[i];
     p->x_off[i + 1] = starts ? span : p->x_off[i] + len;
-    const int64_t outn = fam ? (int64_t)Np * Np * sz : (int64_t)Np * sz;
-    p->out_off[i + 1] = p->out_off[i] + outn;
     p->ws_off[i + 1] = p->ws_off[i] + (int64_t)Np * sz;
   }
+  layout_outputs(p);
   // tables
   if (!(p->tw_np = table_pass(Np, &e)) || !(p->hamming = table_hamming(Np, &e)) ||
       !(p->err = device_error_word(&e))) {
@@ -580,8 +362,7 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
   }
   p->smem = smem_of(fam, tc);
   int per_sm = 0;
-  e = fam ? (tc ? prepare_kernel<true, true>(p->smem, &per_sm) : prepare_kernel<true, false>(p->smem, &per_sm))
-          : (tc ? prepare_kernel<false, true>(p->smem, &per_sm) : prepare_kernel<false, false>(p->smem, &per_sm));
+  e = prepare_kernel(fam, tc, false, p->smem, &per_sm);
   if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
   int sms = 0;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) {
@@ -668,12 +449,17 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   A.counters = p->d_counters; A.x = (const float2*)x_arena; A.y = A.x; A.conj = 0; A.pad_ = 0;
   A.out = (float2*)out_arena; A.ws = (float2*)workspace;
   A.window = w; A.tw_np = p->tw_np; A.bmats_np = p->bm_np; A.bbytes_np = p->bbytes_np; A.err = p->err;
-  const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
+  A.prof_power = p->prof_power; A.pad2_ = 0;
+  const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16, prof = p->prof_power != 0;
+  const int grid = prof ? p->grid_prof : p->grid;
   const size_t cbytes = sizeof(unsigned) * (p->tasks.size() + 1);
+  // profiles are maxima of non-negative values: they start from 0 on every run
+  const size_t pbytes = prof ? sizeof(float) * (size_t)p->out_off[p->nsig] : 0;
   count_launches(1);
   if (!st) {                                                    // legacy stream: no capture, plain launch
     if ((e = cudaMemsetAsync(p->d_counters, 0, cbytes, st)) != cudaSuccess) return cuda_status(e);
-    e = launch_batch(fam, tc, p->grid, p->smem, A, st);
+    if (prof && (e = cudaMemsetAsync(out_arena, 0, pbytes, st)) != cudaSuccess) return cuda_status(e);
+    e = launch_batch(fam, tc, prof, grid, p->smem, A, st);
     return e == cudaSuccess ? SCD_OK : cuda_status(e);
   }
   if (!p->exec || p->g_x != x_arena || p->g_w != (const void*)w || p->g_out != out_arena || p->g_ws != workspace ||
@@ -682,7 +468,8 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_status(e);
     cudaError_t e1 = cudaMemsetAsync(p->d_counters, 0, cbytes, st);
-    cudaError_t e2 = launch_batch(fam, tc, p->grid, p->smem, A, st);
+    if (e1 == cudaSuccess && prof) e1 = cudaMemsetAsync(out_arena, 0, pbytes, st);
+    cudaError_t e2 = launch_batch(fam, tc, prof, grid, p->smem, A, st);
     e = cudaStreamEndCapture(st, &g);
     if (e1 != cudaSuccess) e = e1;
     if (e2 != cudaSuccess) e = e2;
@@ -696,6 +483,29 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
 }
 
 void scd_batch_plan_destroy(scd_batch_plan* p) { free_plan(p); }
+
+scd_status scd_batch_plan_set_output(scd_batch_plan* p, int32_t mode) {
+  using namespace scd;
+  if (!p || mode < 0 || mode > 2) return SCD_ERR_ARG;
+  const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
+  if (mode && fam) {                                            // the FAM map's band must tile alpha
+    if (2 * (int64_t)p->L > p->Np) return SCD_ERR_UNSUPPORTED;
+    for (int i = 0; i < p->nsig; ++i)
+      if ((p->sizes[i] * p->L) % p->Np) return SCD_ERR_UNSUPPORTED;
+  }
+  if (mode && !p->grid_prof) {
+    int per_sm = 0, sms = 0;
+    cudaError_t e = prepare_kernel(fam, tc, true, p->smem, &per_sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (tc && per_sm > 4) per_sm = 4;
+    p->grid_prof = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  p->prof_power = mode;
+  layout_outputs(p);
+  if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+  return build_tasks(p);
+}
 
 scd_status scd_batch_tune(scd_batch_plan* p, const void* x_arena, const float* window, void* out_arena,
                           void* workspace, void* stream, int32_t reps) {
@@ -796,12 +606,13 @@ scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, in
   BatchArgs A;
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = Np; A.L = 1; A.total = p->total;
   A.counters = counters; A.x = x; A.y = y ? y : x; A.conj = conj ? 1 : 0; A.pad_ = 0;
+  A.prof_power = 0; A.pad2_ = 0;
   A.out = out; A.ws = (float2*)ws;
   A.window = window ? window : p->hamming; A.tw_np = p->tw_np; A.bmats_np = p->bm_np;
   A.bbytes_np = p->bbytes_np; A.err = p->err;
   count_launches(1);
   if ((e = cudaMemsetAsync(counters, 0, cbytes, st)) != cudaSuccess) return cuda_status(e);
-  e = launch_batch(false, precision == SCD_SPLIT_BF16, p->grid, p->smem, A, st);
+  e = launch_batch(false, precision == SCD_SPLIT_BF16, false, p->grid, p->smem, A, st);
   return e == cudaSuccess ? SCD_OK : cuda_status(e);
 }
 

@@ -15,6 +15,12 @@ struct TileShape {
   static constexpr int NT = C * T;                      // threads actually used
 };
 
+// prof[i] = max(prof[i], v) for a non-negative float given by its bits (non-negative floats
+// order like their bit patterns); a fire-and-forget reduction in L2.  (Reading the current
+// value first and skipping the atomic when v cannot raise it measured slower: the dependent
+// load sits on every thread's path.)
+__device__ __forceinline__ void profile_max(unsigned* p, unsigned v) { atomicMax(p, v); }
+
 // Runs the C transforms of one tile in the requested form; for TC the caller has opened the
 // tensor-core context and loaded the B matrices of size M into ctx.bsm.
 template <int M, int C, bool CFAST, bool SYNC_DST, int THREADS, bool TC, class Src, class Dst>
@@ -53,10 +59,13 @@ __device__ __forceinline__ void fam_channelise_tile(float2* sm, TcCtx& ctx, cons
 //   out[kh][lh][qh] = sum_p X[kh][p] conj(Y[lh][p]) W_P^{(q p) mod P}
 // Y = X for the auto estimate, the partner's channeliser output for a cross estimate, and
 // the conjugated one for a conjugate estimate.
-template <int PP, bool TC>
+// PROF: instead of storing S, every kept bin (q in [-Q, Q)) is reduced into the alpha profile
+// prof[ah], ah = (k - l) Q + q + P L, by profile_max of |S|^power.
+template <int PP, bool TC, bool PROF = false>
 __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X,
                                                const float2* __restrict__ Y, int Np, float2* __restrict__ out,
-                                               const float2* __restrict__ tw, int64_t pair0) {
+                                               const float2* __restrict__ tw, int64_t pair0, float* prof = nullptr,
+                                               int PL = 0, int Q = 0, int power = 1) {
   using S = TileShape<PP>;
   // this thread's pair (transforms are t-fast: c = tid / T), resolved once
   const int64_t pair = pair0 + (int)threadIdx.x / S::T;
@@ -64,12 +73,21 @@ __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const flo
   const int kh = valid ? (int)(pair / Np) : 0, lh = valid ? (int)(pair % Np) : 0;
   const float2* __restrict__ xk = X + (int64_t)kh * PP;
   const float2* __restrict__ xl = Y + (int64_t)lh * PP;
-  float2* __restrict__ o = out + pair * PP;
+  float2* __restrict__ o = PROF ? nullptr : out + pair * PP;
   auto src = [&](int, int p) -> float2 {
     return valid ? cmulc(__ldg(xk + p), __ldg(xl + p)) : make_float2(0.f, 0.f);
   };
   auto dst = [&](int, int f, float2 v) {
-    if (valid) o[(f + PP / 2) & (PP - 1)] = v;
+    if constexpr (PROF) {
+      const int q = ((f + PP / 2) & (PP - 1)) - PP / 2;
+      if (valid && q >= -Q && q < Q) {
+        const float m2 = fmaf(v.x, v.x, v.y * v.y);
+        profile_max(reinterpret_cast<unsigned*>(prof) + ((kh - lh) * Q + q + PL),
+                    __float_as_uint(power == 2 ? m2 : sqrtf(m2)));
+      }
+    } else {
+      if (valid) o[(f + PP / 2) & (PP - 1)] = v;
+    }
   };
   tile_fft<PP, S::C, false, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
@@ -146,9 +164,13 @@ __host__ __device__ constexpr int rows_stage_bytes() { return M2 * (TileShape<M2
 // SLOT: the input rows are a rotating slot of the persistent schedule, dead once read: their
 // L2 lines are discarded (never written back), and the output is stored with the streaming
 // hint so that it does not push the live slots out of L2.
-template <int M2, bool TC, bool SLOT = false>
+// PROF: instead of storing S, every bin is reduced into the alpha profile prof[sh + ah_off]
+// (ah_off = k N/Np + N/2 for channel k) by profile_max of |S|^power; the transposed order
+// makes each warp's reads and reductions hit consecutive words.
+template <int M2, bool TC, bool SLOT = false, bool PROF = false>
 __device__ __forceinline__ void ssca_rows_tile(float2* sm, TcCtx& ctx, const float2* in, float2* __restrict__ out,
-                                               int M1, const float2* __restrict__ tw, int r0) {
+                                               int M1, const float2* __restrict__ tw, int r0, float* prof = nullptr,
+                                               int ah_off = 0, int power = 1) {
   using S = TileShape<M2>;
   constexpr int C = S::C;
   const float2* __restrict__ rowp = in + (int64_t)(r0 + (int)threadIdx.x / S::T) * M2;   // t-fast: c = tid / T
@@ -160,6 +182,16 @@ __device__ __forceinline__ void ssca_rows_tile(float2* sm, TcCtx& ctx, const flo
     const char* base = reinterpret_cast<const char*>(in + (int64_t)r0 * M2);
     for (int l = threadIdx.x; l < C * M2 * 8 / 128; l += blockDim.x)
       asm volatile("discard.global.L2 [%0], 128;" :: "l"(base + (int64_t)l * 128) : "memory");
+  }
+  if constexpr (PROF) {
+    unsigned* __restrict__ pr = reinterpret_cast<unsigned*>(prof) + ah_off + r0;
+    for (int e = threadIdx.x; e < C * M2; e += blockDim.x) {
+      const int c = e % C, f = e / C;
+      const float2 v = sm[f * (C + 1) + c];
+      const float m2 = fmaf(v.x, v.x, v.y * v.y);
+      profile_max(pr + c + M1 * ((f + M2 / 2) & (M2 - 1)), __float_as_uint(power == 2 ? m2 : sqrtf(m2)));
+    }
+    return;
   }
   float2* __restrict__ o = out + r0;
   for (int e = threadIdx.x; e < C * M2; e += blockDim.x) {
