@@ -267,6 +267,31 @@ class BatchWorkload:
     def stage_times(self, marks):
         return {"fam_batch": marks[0].elapsed_time(marks[1]), "ssca_batch": marks[1].elapsed_time(marks[2])}
 
+    def parity_sample(self, stream):
+        """Error of both forms on the signals whose oracle estimates the CPU-baseline leg just
+        computed: max and mean |S_gpu - S_oracle| / max|S_oracle| per estimator (one fresh run
+        of each plan, outside any timing)."""
+        import numpy as np
+        res = {}
+        for prec in ("fp32", "split"):
+            fam, ssca = self.plans[prec]
+            fam.run(self.x, self.out_f, self.ws, stream=stream)
+            ssca.run(self.x, self.out_s, self.ws, stream=stream)
+            stream.synchronize()
+            self.binding.scd_check_device(stream)
+            for name, plan, out, k in (("fam", fam, self.out_f, 0), ("ssca", ssca, self.out_s, 1)):
+                mx = mean = 0.0
+                for i, refs in self.oracle_refs.items():
+                    ref = refs[k]
+                    d = np.abs(plan.output(out, i).cpu().numpy() - ref)
+                    scale = float(np.max(np.abs(ref)))
+                    mx = max(mx, float(d.max()) / scale)
+                    mean = max(mean, float(d.mean()) / scale)
+                res[f"{name}_{prec}"] = {"max_rel": mx, "mean_rel": mean}
+        res["signals"] = sorted(int(i) for i in self.oracle_refs)
+        res["metric"] = "max (and mean) |S_gpu - S_oracle| / max|S_oracle| over each sampled signal's full estimate"
+        return res
+
     def profile_mode(self, torch, binding, stream, reps=10, warmup=3):
         """The same step with the plans' alpha-profile output (the estimates are reduced to one
         float per alpha column inside the kernels and never written): FP32 form, CUDA events
@@ -335,6 +360,7 @@ class BatchWorkload:
         order = np.argsort(self.lengths)
         pick = [int(order[len(order) * (k + 1) // (nsig + 1)]) for k in range(nsig)]
         af, as_ = orc.hamming_window(self.FAM_NP), orc.hamming_window(self.SSCA_NP)
+        self.oracle_refs = {}
         used = 0
         t0 = time.perf_counter()
         for i in pick:
@@ -346,8 +372,8 @@ class BatchWorkload:
                 orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP, channels=np.arange(0, self.SSCA_NP, 4))
                 used += N // 4
             else:
-                orc.fam(self.sigs[i], af, self.FAM_NP, self.FAM_L, P)
-                orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP)
+                self.oracle_refs[i] = (orc.fam(self.sigs[i], af, self.FAM_NP, self.FAM_L, P),
+                                       orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP))
                 used += (P - 1) * self.FAM_L + self.FAM_NP + N
         t = time.perf_counter() - t0
         what = "a quarter of the FAM pairs and SSCA channels" if reduced else "full FAM and SSCA estimates"
@@ -755,6 +781,9 @@ def run_ours(args):
         t, desc = wl.oracle_sample()
         line["cpu_baseline"] = {"value": wl.samples_per_step() / t / 1e6, "unit": "Msamples/s", "cores": 1,
                                 "kind": "oracle", "sample": desc + "; numpy FFT and elementwise kernels on one thread"}
+        if getattr(wl, "oracle_refs", None):
+            with torch.cuda.stream(stream):
+                line["cpu_baseline"]["parity"] = wl.parity_sample(stream)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

