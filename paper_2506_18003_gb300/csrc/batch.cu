@@ -37,11 +37,6 @@ template <bool FAM, bool TC>
 cudaError_t prepare_one(int smem, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_batch<FAM, TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  // ask for the largest shared-memory carveout, so that two CTAs of the larger (tensor-core)
-  // layouts fit on one SM
-  e = cudaFuncSetAttribute(k_batch<FAM, TC, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<FAM, TC, false>, kThreads, smem);
 }
 }  // namespace
