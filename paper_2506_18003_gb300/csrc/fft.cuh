@@ -67,12 +67,15 @@ template <int M> struct PlanInfo {
   // s sits at off(s) + r p(s) + k and holds W_{p R}^{k r}
   static constexpr int off(int s) { return s <= 1 ? 0 : r0 * r1; }
   static constexpr int tw_len() { return n == 1 ? 1 : (n == 2 ? r0 * r1 : r0 * r1 + r0 * r1 * r2); }
-  // shared-memory stride (complex elements) of one transform: one pad element per 16 and a
-  // stride of 1 mod 16 so that transforms laid side by side fall in different banks
-  static constexpr int stride() { return M + M / 16 + 1; }
+  // shared-memory position of exchange index i: one pad element after every r0 elements, so
+  // that the 16 threads of a half-warp storing their r0 pass-0 outputs (index t r0 + j) hit
+  // 16 different banks (odd stride r0 + 1), and consecutive indices stay consecutive
+  static constexpr int lr0 = r0 >= 32 ? 5 : (r0 >= 16 ? 4 : (r0 >= 8 ? 3 : (r0 >= 4 ? 2 : 1)));
+  __host__ __device__ static constexpr int pad(int i) { return i + (i >> lr0); }
+  // shared-memory stride (complex elements) of one transform: an odd number, so that
+  // transforms laid side by side fall in different banks
+  static constexpr int stride() { return M + M / r0 + 1; }
 };
-
-__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 
 // ----------------------------------------------------------------------------- radix-R DFT
 // W_32^j for j < 16 (cos, -sin), double literals rounded to float at compile time.
@@ -183,7 +186,7 @@ struct FftPieces {
   __host__ __device__ __forceinline__ static void pass0_store(int t, float2* reg, const float2* v) {
     constexpr int R = PI::r0;
 #pragma unroll
-    for (int j = 0; j < R; ++j) reg[spad(t * R + j)] = v[j];
+    for (int j = 0; j < R; ++j) reg[PI::pad(t * R + j)] = v[j];
   }
   // pass S >= 1: load from shared memory with twiddles and run the DFTs
   template <int S>
@@ -195,7 +198,7 @@ struct FftPieces {
       const int k = i & (p - 1);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        float2 x = reg[spad(i + r * (M / R))];
+        float2 x = reg[PI::pad(i + r * (M / R))];
         if (r > 0) x = cmul(x, SCD_LDG(tw + PI::off(S) + r * p + k));
         v[b * R + r] = x;
       }
@@ -211,7 +214,7 @@ struct FftPieces {
       const int i = t + b * T;
       const int k = i & (p - 1);
 #pragma unroll
-      for (int j = 0; j < R; ++j) reg[spad((i - k) * R + k + p * j)] = v[b * R + j];
+      for (int j = 0; j < R; ++j) reg[PI::pad((i - k) * R + k + p * j)] = v[b * R + j];
     }
   }
   // outputs of the last pass S to the consumer (bin f in natural order)

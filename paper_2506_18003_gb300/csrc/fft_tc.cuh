@@ -235,7 +235,7 @@ __device__ __forceinline__ void fft_batch_tc(float2* __restrict__ sm, const floa
         const int k = i & (p - 1);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          float2 x = reg[spad(i + r * (M / R))];
+          float2 x = reg[PI::pad(i + r * (M / R))];
           if (r > 0) x = cmul(x, SCD_LDG(tw + PI::off(1) + r * p + k));
           v[b * R + r] = x;
         }
@@ -258,7 +258,7 @@ __device__ __forceinline__ void fft_batch_tc(float2* __restrict__ sm, const floa
           const int k = i & (p - 1);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            float2 x = reg[spad(i + r * (M / R))];
+            float2 x = reg[PI::pad(i + r * (M / R))];
             if (r > 0) x = cmul(x, SCD_LDG(tw + PI::off(2) + r * p + k));
             v[b * R + r] = x;
           }
