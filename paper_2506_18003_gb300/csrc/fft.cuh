@@ -72,9 +72,11 @@ template <int M> struct PlanInfo {
   // 16 different banks (odd stride r0 + 1), and consecutive indices stay consecutive
   static constexpr int lr0 = r0 >= 32 ? 5 : (r0 >= 16 ? 4 : (r0 >= 8 ? 3 : (r0 >= 4 ? 2 : 1)));
   __host__ __device__ static constexpr int pad(int i) { return i + (i >> lr0); }
-  // shared-memory stride (complex elements) of one transform: an odd number, so that
-  // transforms laid side by side fall in different banks
-  static constexpr int stride() { return M + M / r0 + 1; }
+  // shared-memory stride (complex elements) of one of C transforms laid side by side: the
+  // 16 lanes of a half-warp touch min(C, 16) transforms at 16 / min(C, 16) consecutive
+  // positions each, so the stride is 1 mod 16 for C >= 16 and 16 / C mod 16 below (M + M/r0 is
+  // a multiple of 16 whenever C < 16), which puts every lane in its own bank
+  static constexpr int stride(int C) { return M + M / r0 + (C >= 16 ? 1 : 16 / C); }
 };
 
 // ----------------------------------------------------------------------------- radix-R DFT
@@ -256,7 +258,7 @@ __device__ __forceinline__ void team_sync() {
 // C transforms of size M per CTA, T = M/E threads each (blockDim.x == C*T).
 // CFAST: thread tid works on transform c = tid % C (transforms interleaved across lanes,
 // good when consecutive transforms touch consecutive addresses); otherwise c = tid / T
-// (a transform's threads are consecutive).  `sm` holds C regions of PlanInfo<M>::stride()
+// (a transform's threads are consecutive).  `sm` holds C regions of PlanInfo<M>::stride(C)
 // complex values; `tw` is the concatenated pass-twiddle table for size M.
 //   src(c, idx)      -> float2   input idx of transform c (idx in [0, M))
 //   dst(c, f, value)             output bin f (natural order) of transform c
@@ -272,7 +274,7 @@ __device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2*
   const int tid = threadIdx.x;
   const int c = CFAST ? (tid % C) : (tid / T);
   const int t = CFAST ? (tid / C) : (tid % T);
-  float2* reg = sm + c * PI::stride();
+  float2* reg = sm + c * PI::stride(C);
   float2 v[E];
   F::pass0_load(c, t, src, v);
   if constexpr (PI::n == 1) {

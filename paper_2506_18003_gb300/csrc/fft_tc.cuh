@@ -200,7 +200,7 @@ __device__ __forceinline__ void tc_dft(float2* v, unsigned char* abuf, const uns
 }
 
 // Same contract as fft_batch (fft.cuh) with THREADS == blockDim.x, plus the tensor-core
-// context; `sm` must hold max(C * stride(M) * 8, TcPlan::max_abytes()) bytes.
+// context; `sm` must hold max(C * stride(C) * 8, TcPlan::max_abytes()) bytes.
 template <int M, int C, bool CFAST, bool SYNC_DST, int THREADS, class Src, class Dst>
 __device__ __forceinline__ void fft_batch_tc(float2* __restrict__ sm, const float2* __restrict__ tw, Src& src,
                                              Dst& dst, TcCtx& ctx) {
@@ -212,7 +212,7 @@ __device__ __forceinline__ void fft_batch_tc(float2* __restrict__ sm, const floa
   const int tid = threadIdx.x;
   const int c = CFAST ? (tid % C) : (tid / T);
   const int t = CFAST ? (tid / C) : (tid % T);
-  float2* reg = sm + c * PI::stride();
+  float2* reg = sm + c * PI::stride(C);
   unsigned char* abuf = reinterpret_cast<unsigned char*>(sm);
   float2 v[E];
   // pass 0: inputs straight from the producer
@@ -290,7 +290,7 @@ template <int M, int C, int THREADS, bool TC, int EXTRA = 0>
 struct FftSmem {
   static constexpr int up128(int v) { return (v + 127) / 128 * 128; }
   static constexpr int mx(int a, int b) { return a > b ? a : b; }
-  static constexpr int exch = PlanInfo<M>::n == 1 ? 0 : C * PlanInfo<M>::stride() * 8;
+  static constexpr int exch = PlanInfo<M>::n == 1 ? 0 : C * PlanInfo<M>::stride(C) * 8;
   static constexpr int region0 = up128(mx(mx(exch, EXTRA), TcSizes<M, THREADS, TC>::abytes));
   static constexpr int bbytes = TcSizes<M, THREADS, TC>::bbytes;
   // (tensor-core form: 4 KB of slack after the descriptors' farthest reach)

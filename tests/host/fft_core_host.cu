@@ -28,7 +28,7 @@ double check_size(std::mt19937_64& g) {
     const double ang = 2.0 * M_PI * (double)pass_twiddle_exponent(e, M, PI::r0, PI::r1, PI::r2) / M;
     tw[e] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
   }
-  std::vector<float2> sm(PI::stride() + 16);
+  std::vector<float2> sm(PI::stride(1) + 16);
   std::vector<float2> out(M, make_float2(NAN, NAN));
   std::vector<std::vector<float2>> v(T, std::vector<float2>(E));
   auto src = [&](int c, int i) -> float2 { (void)c; return x[i]; };
