@@ -85,12 +85,16 @@ struct BatchSmem {
               mx(mx(FS<256>::bbytes, FS<512>::bbytes),
                  mx(mx(FS<1024>::bbytes, FS<2048>::bbytes), mx(FS<4096>::bbytes, FS<8192>::bbytes))));
   }
+  static constexpr int cdp_r0() {
+    return mx(mx(CdpSmem<16, TC>::region0, CdpSmem<32, TC>::region0),
+              mx(mx(CdpSmem<64, TC>::region0, CdpSmem<128, TC>::region0), CdpSmem<256, TC>::region0));
+  }
   static constexpr int ssca_r0() {
-    return mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
+    return mx(cdp_r0(), mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
               mx(mx(FS<256>::region0, FS<512>::region0),
                  mx(mx(FS<1024>::region0, FS<64, rows_stage_bytes<64>()>::region0),
                     mx(mx(FS<128, rows_stage_bytes<128>()>::region0, FS<256, rows_stage_bytes<256>()>::region0),
-                       mx(FS<512, rows_stage_bytes<512>()>::region0, FS<1024, rows_stage_bytes<1024>()>::region0)))));
+                       mx(FS<512, rows_stage_bytes<512>()>::region0, FS<1024, rows_stage_bytes<1024>()>::region0))))));
   }
   static constexpr int ssca_b() {
     return mx(mx(mx(FS<16>::bbytes, FS<32>::bbytes), mx(FS<64>::bbytes, FS<128>::bbytes)),
@@ -148,7 +152,7 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
   if (t.op == OP_SSCA_CDP) {
     load_b<TC>(ctx, bsm, A.bmats_np, A.bbytes_np, loaded);
     switch (A.Np) {
-#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, A.y + t.x_off, A.conj != 0, t.N, A.window, A.tw_np, ws, (int)tile * TileShape<NPV>::C); break;
+#define SCD_CD(NPV) case NPV: ssca_cdp_tile<NPV, TC>(sm, ctx, x, A.y + t.x_off, A.conj != 0, t.N, A.window, A.tw_np, ws, (int)tile * TileShape<NPV>::C, reinterpret_cast<unsigned char*>(sm) + CdpStage<NPV, TC>::off); break;
       SCD_CD(16) SCD_CD(32) SCD_CD(64) SCD_CD(128) SCD_CD(256)
 #undef SCD_CD
     }

@@ -29,11 +29,11 @@ k_ssca_cdp(const float2* __restrict__ x, const float2* __restrict__ y, int conj,
            const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<NP>;
-  using FS = FftSmem<NP, S::C, S::NT, TC>;
+  using FS = CdpSmem<NP, TC>;
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  ssca_cdp_tile<NP, TC>(sm, ctx, x, y, conj != 0, N, a, tw, Xg, blockIdx.x * S::C);
+  ssca_cdp_tile<NP, TC>(sm, ctx, x, y, conj != 0, N, a, tw, Xg, blockIdx.x * S::C, base + CdpStage<NP, TC>::off);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
@@ -90,7 +90,7 @@ cudaError_t tc_args(bool tc, int M, TcArgs* a) {
 template <int NPV, bool TC>
 cudaError_t launch_cdp_t(const float2* x, const float2* y, int conj, int N, const float* a, const float2* tw, float2* Xg, TcArgs t, cudaStream_t st) {
   using S = TileShape<NPV>;
-  constexpr int sm = FftSmem<NPV, S::C, S::NT, TC>::total;
+  constexpr int sm = CdpSmem<NPV, TC>::total;
   cudaError_t e = set_smem(k_ssca_cdp<NPV, TC>, sm);
   if (e != cudaSuccess) return e;
   k_ssca_cdp<NPV, TC><<<N / S::C, S::NT, sm, st>>>(x, y, conj, N, a, tw, Xg, t.bm, t.err);

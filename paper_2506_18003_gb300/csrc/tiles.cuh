@@ -96,27 +96,47 @@ __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const flo
 // time points n0 .. n0 + C - 1:  X_g[kh][n] = W_Np^{(k s) mod Np} DFT_Np(a x[s ..])[k] conj(y[n])
 // (y = x for the auto estimate; conj: y[n] itself, the conjugate estimate).  As in K1 the
 // down-conversion is the placement of a[r] x[s+r] at FFT input position (s + r) mod Np.
+// The tile's C + Np - 1 input samples (zero outside [0, N)) and the window are staged in
+// shared memory first (`stage`, cdp_stage_bytes<NP>() bytes, disjoint from the FFT's
+// exchange and tensor-core buffers): the C transforms read the same samples at shifted
+// window positions, so every lane of a half-warp then reads one broadcast word.
+template <int NP>
+__host__ __device__ constexpr int cdp_stage_bytes() { return (TileShape<NP>::C + NP) * 8 + NP * 4; }
+
+// Layout of a CTA running K3 tiles: the FFT's exchange / tensor-core buffers, then the
+// staging area at `off`, all inside region 0 (the split form's B matrices follow region 0).
+template <int NP, bool TC>
+struct CdpStage {
+  static constexpr int off = FftSmem<NP, TileShape<NP>::C, TileShape<NP>::NT, TC>::region0;
+  static constexpr int end = off + cdp_stage_bytes<NP>();
+};
+template <int NP, bool TC>
+using CdpSmem = FftSmem<NP, TileShape<NP>::C, TileShape<NP>::NT, TC, CdpStage<NP, TC>::end>;
+
 template <int NP, bool TC>
 __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x,
                                               const float2* __restrict__ y, bool conj, int N,
                                               const float* __restrict__ a, const float2* __restrict__ tw,
-                                              float2* __restrict__ Xg, int n0) {
+                                              float2* __restrict__ Xg, int n0, unsigned char* stage) {
   using S = TileShape<NP>;
+  float2* xs = reinterpret_cast<float2*>(stage);
+  float* as = reinterpret_cast<float*>(stage + (S::C + NP) * 8);
+  for (int i = threadIdx.x; i < S::C + NP; i += blockDim.x) {
+    const int m = n0 - NP / 2 + i;
+    xs[i] = (m >= 0 && m < N) ? __ldg(x + m) : make_float2(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) as[i] = __ldg(a + i);
   // this thread's time point (transforms interleaved: c = tid % C), resolved once
-  const int n = n0 + (int)threadIdx.x % S::C;
-  const bool interior = n0 - NP / 2 >= 0 && n0 + S::C + NP / 2 <= N;   // whole tile away from the ends
-  const int s = n - NP / 2;                                         // window start (may be < 0)
-  const int smod = s & (NP - 1);
+  const int c = (int)threadIdx.x % S::C;
+  const int n = n0 + c;
+  const int smod = (n - NP / 2) & (NP - 1);                         // window start mod Np
   float2 xn = __ldg(y + n);                                         // the factor is conj(xn)
   if (conj) xn.y = -xn.y;
   float2* __restrict__ o = Xg + n;
+  __syncthreads();                                                  // staged samples visible
   auto src = [&](int, int j) -> float2 {
     const int r = (j - smod) & (NP - 1);                            // j = (s + r) mod Np
-    if (!interior) {
-      const int m = s + r;
-      if (m < 0 || m >= N) return make_float2(0.f, 0.f);
-    }
-    return cscale(__ldg(x + (s + r)), __ldg(a + r));
+    return cscale(xs[c + r], as[r]);
   };
   auto dst = [&](int, int f, float2 v) { o[(int64_t)((f + NP / 2) & (NP - 1)) * N] = cmulc(v, xn); };
   tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
