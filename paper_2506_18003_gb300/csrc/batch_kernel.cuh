@@ -86,8 +86,10 @@ struct BatchSmem {
                  mx(mx(FS<1024>::bbytes, FS<2048>::bbytes), mx(FS<4096>::bbytes, FS<8192>::bbytes))));
   }
   static constexpr int cdp_r0() {
-    return mx(mx(CdpSmem<16, TC>::region0, CdpSmem<32, TC>::region0),
-              mx(mx(CdpSmem<64, TC>::region0, CdpSmem<128, TC>::region0), CdpSmem<256, TC>::region0));
+    return mx(mx(mx(CdpSmem<16, TC>::region0, CdpSmem<32, TC>::region0),
+                 mx(mx(CdpSmem<64, TC>::region0, CdpSmem<128, TC>::region0), CdpSmem<256, TC>::region0)),
+              mx(mx(mx(ColsSmem<64, TC>::region0, ColsSmem<128, TC>::region0), ColsSmem<256, TC>::region0),
+                 mx(ColsSmem<512, TC>::region0, ColsSmem<1024, TC>::region0)));
   }
   static constexpr int ssca_r0() {
     return mx(cdp_r0(), mx(mx(mx(FS<16>::region0, FS<32>::region0), mx(FS<64>::region0, FS<128>::region0)),
@@ -166,7 +168,8 @@ __device__ __forceinline__ void ssca_tile(const BatchArgs& A, const Task& t, int
     const int per = t.M2 / C;                                                               \
     const int64_t kh = tile / per;                                                          \
     ssca_cols_tile<MV, TC, true>(sm, ctx, ws + (t.ch0 + kh) * t.N, A.ws + t.mid_off + kh * t.N, t.N, t.M2, t.wN, \
-                           t.cols, t.tw, (int)(tile % per) * C);                            \
+                           t.cols, t.tw, (int)(tile % per) * C,                             \
+                           reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(sm) + ColsStage<MV, TC>::off)); \
   } break;
       SCD_CO(64) SCD_CO(128) SCD_CO(256) SCD_CO(512) SCD_CO(1024)
 #undef SCD_CO

@@ -43,12 +43,13 @@ k_ssca_cols(float2* __restrict__ Y, int N, int M2, const float2* __restrict__ wN
             const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<M1>;
-  using FS = FftSmem<M1, S::C, S::NT, TC>;
+  using FS = ColsSmem<M1, TC>;
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
   float2* row = Y + (int64_t)blockIdx.y * N;
-  ssca_cols_tile<M1, TC>(sm, ctx, row, row, N, M2, wN, cols, tw, blockIdx.x * S::C);
+  ssca_cols_tile<M1, TC>(sm, ctx, row, row, N, M2, wN, cols, tw, blockIdx.x * S::C,
+                         reinterpret_cast<float2*>(base + ColsStage<M1, TC>::off));
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
@@ -107,7 +108,7 @@ cudaError_t launch_cols_t(float2* Y, int N, int Np, int M1, int M2, TcArgs t, cu
   if (!cols) return err;
   const float2* tw = table_pass(M1, &err);
   if (!tw) return err;
-  constexpr int sm = FftSmem<MV, S::C, S::NT, TC>::total;
+  constexpr int sm = ColsSmem<MV, TC>::total;
   if ((err = set_smem(k_ssca_cols<MV, TC>, sm)) != cudaSuccess) return err;
   k_ssca_cols<MV, TC><<<dim3(M2 / S::C, Np), S::NT, sm, st>>>(Y, N, M2, wN, cols, tw, t.bm, t.err);
   return cudaGetLastError();

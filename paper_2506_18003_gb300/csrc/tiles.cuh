@@ -148,19 +148,36 @@ __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const floa
 // at [m1'][m2].  wN = W_N^j table, cols = W_N^{c m1'} at [m1'][c].
 // DISCARD: the input (X_g) is dead once this tile has read it and `out` is another buffer:
 // the tile's whole L2 lines of it are discarded so that they are never written back.
+// FP32 form: the tile's factors W_N^{m20 f} (f < M1, common to its C columns) are gathered
+// from the W_N table into shared memory (`stage`, M1 values, disjoint from the FFT's buffers)
+// before the transform, whose barriers order them before the last pass reads them.  The split
+// form reads them from the table directly: its larger layout would otherwise outgrow the
+// shared-memory carveout that leaves two CTAs per SM a useful L1.
+template <int M1, bool TC>
+struct ColsStage {
+  static constexpr int off = FftSmem<M1, TileShape<M1>::C, TileShape<M1>::NT, TC>::region0;
+  static constexpr int end = off + (TC ? 0 : M1 * 8);
+};
+template <int M1, bool TC>
+using ColsSmem = FftSmem<M1, TileShape<M1>::C, TileShape<M1>::NT, TC, ColsStage<M1, TC>::end>;
+
 template <int M1, bool TC, bool DISCARD = false>
 __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const float2* in, float2* out, int N, int M2,
                                                const float2* __restrict__ wN, const float2* __restrict__ cols,
-                                               const float2* __restrict__ tw, int m20) {
+                                               const float2* __restrict__ tw, int m20, float2* stage) {
   using S = TileShape<M1>;
   constexpr int C = S::C;
+  static_assert(PlanInfo<M1>::n >= 2, "the staged factors rely on the transform's barriers");
+  if constexpr (!TC)
+    for (int f = threadIdx.x; f < M1; f += blockDim.x) stage[f] = __ldg(wN + ((m20 * f) & (N - 1)));
   const int c = (int)threadIdx.x % C;                             // interleaved columns: c = tid % C
   const float2* ib = in + m20 + c;
   float2* ob = out + m20 + c;
   const float2* __restrict__ colc = cols + c;
   auto src = [&](int, int m1) -> float2 { return ib[(int64_t)m1 * M2]; };
   auto dst = [&](int, int f, float2 v) {
-    const float2 w = cmul(__ldg(wN + ((m20 * f) & (N - 1))), __ldg(colc + f * C));  // W_N^{(m20+c) f}
+    const float2 wm = TC ? __ldg(wN + ((m20 * f) & (N - 1))) : stage[f];
+    const float2 w = cmul(wm, __ldg(colc + f * C));               // W_N^{(m20+c) f}
     ob[(int64_t)f * M2] = cmul(v, w);
   };
   tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
