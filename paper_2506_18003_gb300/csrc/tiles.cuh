@@ -167,9 +167,7 @@ __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const flo
                                                const float2* __restrict__ tw, int m20, float2* stage) {
   using S = TileShape<M1>;
   constexpr int C = S::C;
-  // the factors are read in the last pass by any thread: the interleaved layout's team
-  // barrier (the CTA barrier, team_sync<T, true>) after pass 0 orders them after the writes
-  static_assert(PlanInfo<M1>::n >= 2, "the staged factors rely on the transform's CTA-wide barriers");
+  static_assert(PlanInfo<M1>::n >= 2, "the staged factors rely on the transform's barriers");
   if constexpr (!TC)
     for (int f = threadIdx.x; f < M1; f += blockDim.x) stage[f] = __ldg(wN + ((m20 * f) & (N - 1)));
   const int c = (int)threadIdx.x % C;                             // interleaved columns: c = tid % C
