@@ -162,3 +162,42 @@ def test_map_of_exact_oracle_input_is_exact(torch):
     ref = orc.fam_map(S.astype(np.complex128), Np, L, P)
     assert _rel(got, ref) < 1e-6
     assert np.array_equal(got == 0, ref == 0)
+
+
+# ----------------------------------------------------------------------------- maximum sizes
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_fam_maximum_size_sampled_pairs(torch, precision):
+    """The largest FAM the ABI takes at the largest Np: Np=256, P=16384 (L=64, N = 1,048,768;
+    an 8.6 GB estimate): 12 sampled channel pairs recomputed by the oracle."""
+    Np, L, P = 256, 64, 16384
+    N = (P - 1) * L + Np
+    x = signals.modulated("qpsk", N, 4, 0.07, 10.0, seed=9100)
+    a = orc.hamming_window(Np)
+    got_t = binding.scd_fam(_dev(torch, x), Np, L, P, window=_dev(torch, a), precision=precision)
+    kh = np.array([0, 255, 128, 17, 200, 64, 3, 250, 128, 90, 0, 255])
+    lh = np.array([0, 255, 128, 230, 5, 64, 3, 6, 127, 91, 255, 0])
+    ref = orc.fam_pairs(x, a, Np, L, P, kh, lh)
+    got = got_t[torch.from_numpy(kh).cuda(), torch.from_numpy(lh).cuda()].cpu().numpy()
+    smax = float(np.max(np.abs(got_t[torch.arange(Np), torch.arange(Np), P // 2].cpu().numpy())))
+    tol = FP32_TOL if precision == "fp32" else 1e-3
+    assert float(np.max(np.abs(got - ref))) / smax <= tol
+    del got_t
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("Np", [16, 64])
+def test_ssca_maximum_length_small_np(torch, Np):
+    """N = 2^20 with the smallest channel counts (single-pass 16-point channeliser at Np=16):
+    4 full channel rows recomputed by the oracle."""
+    N = 1 << 20
+    x = signals.modulated("bpsk", N, 4, -0.12, 3.0, seed=9200 + Np)
+    a = orc.hamming_window(Np)
+    got_t = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a))
+    binding.scd_check_device()
+    ch = np.array([0, Np // 2 - 1, Np // 2, Np - 1])
+    ref = orc.ssca(x, a, Np, channels=ch, chunk=1 << 16)
+    got = got_t[torch.from_numpy(ch).cuda()].cpu().numpy()
+    smax = got_t.abs().max().item()
+    assert float(np.max(np.abs(got - ref))) / smax <= FP32_TOL
+    del got_t
+    torch.cuda.empty_cache()
