@@ -91,6 +91,7 @@ size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision) {
 
 scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window, void* out,
                    const scd_opts* opts) {
+  scd::NvtxRange range("scd_fam");
   scd_status s = check_fam(x, N, Np, L, P, window, out);
   if (s != SCD_OK) return s;
   const scd_opts& o = opts_or_default(opts);
@@ -99,6 +100,7 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
   const size_t need = scd_fam_workspace_bytes(N, Np, L, P, o.precision);
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
+  if (scd::fault_host("fam")) return SCD_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)o.stream;
   cudaError_t e;
   if (!window) {
@@ -129,6 +131,7 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
 }
 
 scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, void* out, const scd_opts* opts) {
+  scd::NvtxRange range("scd_ssca");
   scd_status s = check_ssca(x, N, Np, window, out);
   if (s != SCD_OK) return s;
   const scd_opts& o = opts_or_default(opts);
@@ -139,6 +142,7 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   const size_t need = scd_ssca_workspace_bytes(N, Np, o.precision);
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
+  if (scd::fault_host("ssca")) return SCD_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)o.stream;
   cudaError_t e;
   if (!window) {
@@ -209,8 +213,10 @@ scd_status run_one(const scd_opts& o, Launch launch) {
 extern "C" {
 
 scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts) {
+  scd::NvtxRange range("scd_fam_map");
   scd_status s = check_fam_grid(S, Np, L, P, map);
   if (s != SCD_OK) return s;
+  if (scd::fault_host("fam_map")) return SCD_ERR_CUDA;
   const scd_opts& o = opts_or_default(opts);
   return run_one(o, [&](cudaStream_t st) {
     return scd::fam_map((const float2*)S, Np, L, P, o.map_power, o.conjugate != 0, map, st);
@@ -237,8 +243,10 @@ scd_status scd_ssca_alpha_profile(const void* S, int64_t N, int32_t Np, float* p
 }
 
 scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts) {
+  scd::NvtxRange range("scd_ssca_map");
   scd_status s = check_ssca_grid(S, N, Np, map);
   if (s != SCD_OK) return s;
+  if (scd::fault_host("ssca_map")) return SCD_ERR_CUDA;
   const scd_opts& o = opts_or_default(opts);
   return run_one(o, [&](cudaStream_t st) { return scd::ssca_map((const float2*)S, N, Np, o.map_power, map, st); });
 }

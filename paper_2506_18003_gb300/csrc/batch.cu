@@ -104,6 +104,7 @@ struct scd_batch_plan {
   const void* g_out = nullptr;
   const void* g_ws = nullptr;
   void* g_stream = nullptr;
+  int g_drop = -1;
   // streaming plans (scd_stream_plan_create): window length and hop; 0 for batches
   int64_t stream_window = 0, stream_hop = 0;
   // output mode (scd_batch_plan_set_output): 0 full estimates, 1 / 2 alpha profiles of |S|^1 / |S|^2
@@ -440,10 +441,12 @@ scd_status scd_batch_query(const scd_batch_plan* p, int64_t* x_offsets, int64_t*
 scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* window, void* out_arena, void* workspace,
                          void* stream) {
   using namespace scd;
+  NvtxRange range("scd_batch_run");
   if (!p || !x_arena || !out_arena || !workspace) return SCD_ERR_ARG;
   if (((uintptr_t)x_arena % 8) || ((uintptr_t)out_arena % 16) || ((uintptr_t)workspace % 16) ||
       (window && ((uintptr_t)window % 4)))
     return SCD_ERR_ARG;
+  if (fault_host("batch_run")) return SCD_ERR_CUDA;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_status(e);
@@ -455,7 +458,8 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   A.counters = p->d_counters; A.x = (const float2*)x_arena; A.y = A.x; A.conj = 0; A.pad_ = 0;
   A.out = (float2*)out_arena; A.ws = (float2*)workspace;
   A.window = w; A.tw_np = p->tw_np; A.bmats_np = p->bm_np; A.bbytes_np = p->bbytes_np; A.err = p->err;
-  A.prof_power = p->prof_power; A.pad2_ = 0;
+  A.prof_power = p->prof_power;
+  A.drop_task = fault_batch_drop();
   const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16, prof = p->prof_power != 0;
   const int grid = prof ? p->grid_prof : p->grid;
   const size_t cbytes = sizeof(unsigned) * (p->tasks.size() + 1);
@@ -469,7 +473,7 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
     return e == cudaSuccess ? SCD_OK : cuda_status(e);
   }
   if (!p->exec || p->g_x != x_arena || p->g_w != (const void*)w || p->g_out != out_arena || p->g_ws != workspace ||
-      p->g_stream != stream) {
+      p->g_stream != stream || p->g_drop != A.drop_task) {
     if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_status(e);
@@ -483,6 +487,7 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) { p->exec = nullptr; return cuda_status(e); }
     p->g_x = x_arena; p->g_w = w; p->g_out = out_arena; p->g_ws = workspace; p->g_stream = stream;
+    p->g_drop = A.drop_task;
   }
   e = cudaGraphLaunch(p->exec, st);
   return e == cudaSuccess ? SCD_OK : cuda_status(e);
@@ -612,7 +617,8 @@ scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, in
   BatchArgs A;
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = Np; A.L = 1; A.total = p->total;
   A.counters = counters; A.x = x; A.y = y ? y : x; A.conj = conj ? 1 : 0; A.pad_ = 0;
-  A.prof_power = 0; A.pad2_ = 0;
+  A.prof_power = 0;
+  A.drop_task = -1;
   A.out = out; A.ws = (float2*)ws;
   A.window = window ? window : p->hamming; A.tw_np = p->tw_np; A.bmats_np = p->bm_np;
   A.bbytes_np = p->bbytes_np; A.err = p->err;

@@ -28,7 +28,8 @@ struct Task {
 struct BatchArgs {
   const Task* tasks;
   int32_t ntasks, Np, L;
-  int32_t prof_power, pad2_;              // alpha-profile output (1: |S|, 2: |S|^2); 0: full estimates
+  int32_t prof_power;                     // alpha-profile output (1: |S|, 2: |S|^2); 0: full estimates
+  int32_t drop_task;                      // test-time fault injection: never publish this task (-1)
   int64_t total;                          // tiles in the whole plan
   unsigned* counters;                     // [0]: next tile, [1 + t]: tiles of task t done
   const float2* x;                        // x arena
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs A) {
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && s_task != A.drop_task) {
       __threadfence();
       atomicAdd(A.counters + 1 + s_task, 1u);
     }

@@ -86,6 +86,23 @@ scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, in
                                  float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision,
                                  int64_t item_bytes, int64_t slot_bytes);
 
+// ---------------------------------------------------------------- diagnostics (diag.cu)
+// Fault injection for tests, from the environment variable SCD_FAULT_INJECT (read on every
+// call, so a test can set and clear it):
+//   "host:<site>"     the entry point <site> (fam, ssca, fam_map, ssca_map, batch_run) fails
+//                     with SCD_ERR_CUDA and scd_last_error() "injected fault at <site>" after
+//                     its argument checks and before it touches the GPU;
+//   "batch_drop:<t>"  batch runs never publish the completion of task t (0 = the first
+//                     signal's first stage), so the tasks that depend on it give up their
+//                     bounded waits and scd_check_device() reports SCD_ERR_TIMEOUT.
+bool fault_host(const char* site);
+int fault_batch_drop();
+// NVTX range around an entry point (visible to Nsight tools; no cost without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name);
+  ~NvtxRange();
+};
+
 // ---------------------------------------------------------------- launch accounting
 void count_launches(int n);
 // Sets the text scd_last_error() returns on this thread.

@@ -166,3 +166,25 @@ def test_chebyshev_window_validation(lib):
     assert lib.scd_chebyshev_window(64, 0.0, FAKE, None) == binding.SCD_ERR_ARG
     assert lib.scd_chebyshev_window(64, float("nan"), FAKE, None) == binding.SCD_ERR_ARG
     assert lib.scd_chebyshev_window(64, 100.0, None, None) == binding.SCD_ERR_ARG
+
+
+def test_host_fault_injection(lib, monkeypatch):
+    """SCD_FAULT_INJECT=host:<site> makes that entry point fail after its argument checks and
+    before any GPU work, with a message naming the site (no GPU needed)."""
+    o = binding.ScdOpts()
+    o.map_power = 1
+    o.workspace = 1 << 20
+    o.workspace_bytes = 1 << 40
+    monkeypatch.setenv("SCD_FAULT_INJECT", "host:fam")
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_CUDA
+    assert b"injected fault at fam" in lib.scd_last_error()
+    # argument errors still come first
+    assert lib.scd_fam(FAKE, 279, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    monkeypatch.setenv("SCD_FAULT_INJECT", "host:ssca")
+    assert lib.scd_ssca(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_CUDA
+    monkeypatch.setenv("SCD_FAULT_INJECT", "host:ssca_map")
+    assert lib.scd_ssca_map(FAKE, 4096, 32, FAKE, None) == binding.SCD_ERR_CUDA
+    monkeypatch.setenv("SCD_FAULT_INJECT", "host:fam_map")
+    assert lib.scd_fam_map(FAKE, 32, 8, 32, FAKE, None) == binding.SCD_ERR_CUDA
+    monkeypatch.delenv("SCD_FAULT_INJECT")
+    assert lib.scd_fam_map(None, 32, 8, 32, FAKE, None) == binding.SCD_ERR_ARG
