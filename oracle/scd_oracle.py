@@ -45,6 +45,7 @@ __all__ = [
     "hamming_window",
     "chebyshev_window",
     "chebyshev_window64",
+    "input_scale",
     "twiddle",
     "fam_demodulates",
     "fam",
@@ -118,14 +119,27 @@ def _partner(x, y):
     return y
 
 
-def _promote(x, a):
+def _promote(x, a, scale: float = 1.0):
     x = np.asarray(x)
     a = np.asarray(a)
     if x.dtype != np.complex64:
         raise TypeError("x must be complex64 (the bits the GPU path consumes)")
     if a.dtype != np.float32:
         raise TypeError("window must be float32 (the bits the GPU path consumes)")
-    return x.astype(np.complex128), a.astype(np.float64)
+    return x.astype(np.complex128) * scale, a.astype(np.float64)
+
+
+def input_scale(x, used: int, mode: int) -> float:
+    """The factor the `Normalize` step of Algorithm 1 (`Framing`: the norm kernel normalises
+    the input before decimation, Sec. III-A) multiplies the input by, computed in FP64 over
+    the `used` samples the estimate consumes: mode 1 makes their mean power 1
+    (1/sqrt(mean |x|^2)), mode 2 their peak magnitude 1 (1/max |x|), mode 0 leaves the input
+    as it is.  An all-zero input is left as it is."""
+    if mode == 0:
+        return 1.0
+    v = np.asarray(x)[:used].astype(np.complex128)
+    p = np.mean(np.abs(v) ** 2) if mode == 1 else np.max(np.abs(v)) ** 2
+    return 1.0 / np.sqrt(p) if p > 0 else 1.0
 
 
 def _signed_channels(Np: int) -> np.ndarray:
@@ -143,15 +157,16 @@ def _dft_rows(blocks: np.ndarray, M: int, out_bins: np.ndarray, mode: str) -> np
 
 
 # ----------------------------------------------------------------------------- FAM
-def fam_demodulates(x, a, Np: int, L: int, P: int, mode: str = "fft") -> np.ndarray:
+def fam_demodulates(x, a, Np: int, L: int, P: int, mode: str = "fft", scale: float = 1.0) -> np.ndarray:
     """FAM channeliser (Sec. II-B-1, Eq. II.B-complex_demodulate_final, with the block
     framing of Algorithm 1 `Framing`: block p covers x[pL .. pL+Np-1]).
 
         X(p, k) = W_Np^{(k p L) mod Np} * sum_{n<Np} a[n] x[pL + n] W_Np^{(k n) mod Np}
 
-    The first factor is the down-conversion.  Returns complex128 [Np (kh)][P (p)].
+    The first factor is the down-conversion.  `scale` multiplies the input first (input
+    normalisation).  Returns complex128 [Np (kh)][P (p)].
     """
-    x, a = _promote(x, a)
+    x, a = _promote(x, a, scale)
     if x.shape[0] < (P - 1) * L + Np:
         raise ValueError("FAM needs N >= (P-1)*L + Np samples")
     n = np.arange(Np, dtype=np.int64)
@@ -191,10 +206,13 @@ def fam_pairs(x, a, Np: int, L: int, P: int, kh, lh, mode: str = "fft", y=None,
     return _fam_second_fft(z, P, mode)
 
 
-def fam(x, a, Np: int, L: int, P: int, mode: str = "fft", y=None, conjugate: bool = False) -> np.ndarray:
+def fam(x, a, Np: int, L: int, P: int, mode: str = "fft", y=None, conjugate: bool = False,
+        normalise: int = 0) -> np.ndarray:
     """Full FAM estimate, complex128 [Np (kh)][Np (lh)][P (qh)] (y, conjugate: as in
-    fam_pairs)."""
-    X = fam_demodulates(x, a, Np, L, P, mode)
+    fam_pairs; normalise: the input normalisation of input_scale, auto estimate only)."""
+    if normalise and y is not None:
+        raise ValueError("input normalisation is defined for the auto estimate")
+    X = fam_demodulates(x, a, Np, L, P, mode, input_scale(x, (P - 1) * L + Np, normalise))
     Y = X if y is None else fam_demodulates(_partner(x, y), a, Np, L, P, mode)
     second = Y if conjugate else np.conj(Y)
     out = np.empty((Np, Np, P), dtype=np.complex128)
@@ -205,7 +223,7 @@ def fam(x, a, Np: int, L: int, P: int, mode: str = "fft", y=None, conjugate: boo
 
 
 # ----------------------------------------------------------------------------- SSCA
-def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.ndarray:
+def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft", scale: float = 1.0) -> np.ndarray:
     """SSCA channeliser at hop 1 (Sec. II-C; the complex demodulate of Sec. II-A,
     Eq. II.A-complex demodulate, centred on sample n, with the window spanning
     x[n - Np/2 .. n + Np/2 - 1] and x taken as zero outside [0, N)):
@@ -213,9 +231,10 @@ def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.n
         X_T(n, k) = W_Np^{(k s) mod Np} * sum_{r<Np} a[r] x[s + r] W_Np^{(k r) mod Np},
         s = n - Np/2.
 
-    Returns complex128 [len(n)][len(channels)] (channels are stored indices kh).
+    `scale` multiplies the input first (input normalisation).  Returns complex128
+    [len(n)][len(channels)] (channels are stored indices kh).
     """
-    x, a = _promote(x, a)
+    x, a = _promote(x, a, scale)
     N = x.shape[0]
     n = np.asarray(n, dtype=np.int64)
     kh = np.arange(Np, dtype=np.int64) if channels is None else np.asarray(channels, np.int64)
@@ -230,14 +249,14 @@ def ssca_demodulates(x, a, Np: int, n, channels=None, mode: str = "fft") -> np.n
 
 
 def ssca_cdp(x, a, Np: int, n, channels=None, mode: str = "fft", y=None,
-             conjugate: bool = False) -> np.ndarray:
+             conjugate: bool = False, scale: float = 1.0) -> np.ndarray:
     """Channel-data product of Sec. II-C, Eq. Xg with g = 1:
     X_g(n, k) = X_T(n, k) conj(y[n]), y = x for the auto estimate (Sec. II-C multiplies
     the demodulate by the conjugated second signal).  conjugate=True multiplies by y[n]
     itself (the conjugate estimate).  Returns complex128 [len(channels)][len(n)]."""
     n = np.asarray(n, dtype=np.int64)
-    XT = ssca_demodulates(x, a, Np, n, channels, mode)            # [n][ch]
-    yn = np.asarray(_partner(x, y)).astype(np.complex128)[n]
+    XT = ssca_demodulates(x, a, Np, n, channels, mode, scale)     # [n][ch]
+    yn = np.asarray(_partner(x, y)).astype(np.complex128)[n] * scale
     second = yn if conjugate else np.conj(yn)
     return (XT * second[:, None]).T
 
@@ -255,7 +274,7 @@ def ssca_strip(Xg_row: np.ndarray, mode: str = "fft") -> np.ndarray:
 
 
 def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13, y=None,
-         conjugate: bool = False) -> np.ndarray:
+         conjugate: bool = False, normalise: int = 0) -> np.ndarray:
     """SSCA estimate (Sec. II-C, Eq. Xg and Eq. II.B-SSCA_auto, with g = 1 and the
     time origin at the first sample):
 
@@ -268,11 +287,14 @@ def ssca(x, a, Np: int, mode: str = "fft", channels=None, chunk: int = 1 << 13, 
     [len(channels)][N (sh)], sh = q + N/2.
     """
     N = np.asarray(x).shape[0]
+    if normalise and y is not None:
+        raise ValueError("input normalisation is defined for the auto estimate")
+    scale = input_scale(x, N, normalise)                          # input normalisation (Algorithm 1)
     kh = np.arange(Np, dtype=np.int64) if channels is None else np.asarray(channels, np.int64)
     Xg = np.empty((kh.shape[0], N), dtype=np.complex128)          # channel-major CDP
     for n0 in range(0, N, chunk):                                 # channeliser in chunks of time
         n = np.arange(n0, min(N, n0 + chunk), dtype=np.int64)
-        Xg[:, n0:n0 + n.shape[0]] = ssca_cdp(x, a, Np, n, kh, mode, y, conjugate)
+        Xg[:, n0:n0 + n.shape[0]] = ssca_cdp(x, a, Np, n, kh, mode, y, conjugate, scale)
     if mode == "direct":
         return ssca_strip(Xg, mode)                               # one DFT-matrix product
     out = np.empty_like(Xg)
