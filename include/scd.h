@@ -91,6 +91,13 @@ typedef struct {
    * X_T(n,k) y[n]); it correlates x near f1 with y near f2 at alpha = f1 + f2.  Used by
    * scd_fam, scd_ssca, scd_fam_map and scd_fam_alpha_profile; 0 = the paper's estimate. */
   int32_t conjugate;
+  /* Input normalisation (Algorithm 1's Framing stage normalises the input before
+   * decimation; the paper does not say how): 0 = none, 1 = the consumed samples scaled to
+   * mean power 1, 2 = scaled to peak magnitude 1 (an all-zero input is left as it is).  The
+   * estimates are bilinear in x, so this equals S / (mean |x|^2) or S / max |x|^2; it is
+   * applied by scaling the window (two small kernels before the first stage event).  scd_fam
+   * and scd_ssca, auto estimate only (with opts->y: SCD_ERR_UNSUPPORTED). */
+  int32_t normalise;
 } scd_opts;
 
 /* ------------------------------------------------------------------------------ FAM
@@ -108,7 +115,7 @@ typedef struct {
  *   P       blocks, power of two in [2, 16384]
  *   window  float32[Np] or NULL (Hamming)
  *   out     complex64[Np][Np][P], out[kh][lh][qh] = S(k, l, q)
- *   opts    workspace >= scd_fam_workspace_bytes(...) bytes (covers every variant)
+ *   opts    workspace >= scd_fam_workspace_bytes(...) bytes (covers every variant and option)
  * Errors: SCD_ERR_ARG (NULL/misaligned pointers, N too short, L < 1),
  *         SCD_ERR_UNSUPPORTED (Np or P out of range / not a power of two, precision),
  *         SCD_ERR_WORKSPACE, SCD_ERR_CUDA. */
@@ -284,7 +291,8 @@ SCD_API size_t scd_ssca_host_workspace_bytes(int64_t N, int32_t Np, int32_t prec
  * library routine.  Arguments, output and results are those of scd_fam (opts->workspace is
  * ignored), with one more limit: Np * P <= 262144 (e.g. Np = 256 with P <= 1024);
  * larger sizes return SCD_ERR_UNSUPPORTED and scd_last_error() names the limit.  Only the
- * auto estimate: opts->y or opts->conjugate set gives SCD_ERR_UNSUPPORTED.
+ * auto estimate without normalisation: opts->y, opts->conjugate or opts->normalise set gives
+ * SCD_ERR_UNSUPPORTED.
  * All calls share the scratch array, which keeps the last call's contents (each call
  * rewrites everything it reads, so nothing has to start at zero); calls whose executions
  * overlap on the same GPU race on it and must be serialised by the caller.  The first call

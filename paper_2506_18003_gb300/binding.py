@@ -30,6 +30,7 @@ class ScdOpts(ctypes.Structure):
         ("schedule", ctypes.c_int32),
         ("y", ctypes.c_void_p),
         ("conjugate", ctypes.c_int32),
+        ("normalise", ctypes.c_int32),
     ]
 
 
@@ -140,9 +141,13 @@ def _need(t, dtype, numel, name):
 SCHEDULES = {"auto": 0, "stages": 1, "persistent": 2}
 
 
+NORMALISE = {None: 0, "none": 0, "power": 1, "peak": 2}
+
+
 def make_opts(stream=None, precision="fp32", workspace=None, map_power=1, schedule="auto", y=None,
-              conjugate=False) -> ScdOpts:
+              conjugate=False, normalise=None) -> ScdOpts:
     o = ScdOpts()
+    o.normalise = NORMALISE[normalise] if not isinstance(normalise, int) else normalise
     o.stream = _stream(stream)
     o.schedule = SCHEDULES[schedule]
     o.y = None if y is None else y.data_ptr()
@@ -172,9 +177,10 @@ def _partner(x, y):
 
 
 def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32", stream=None, workspace=None,
-            y=None, conjugate=False):
+            y=None, conjugate=False, normalise=None):
     """FAM estimate of the complex64 CUDA tensor x; returns complex64 [Np, Np, P].
-    y: second signal of a cross estimate; conjugate: the conjugate estimate."""
+    y: second signal of a cross estimate; conjugate: the conjugate estimate; normalise:
+    None, "power" (consumed samples scaled to mean power 1) or "peak" (peak magnitude 1)."""
     torch = _torch()
     lib = load()
     _need(x, torch.complex64, 1, "x")
@@ -187,15 +193,16 @@ def scd_fam(x, Np: int, L: int, P: int, window=None, out=None, precision="fp32",
     _need(out, torch.complex64, Np * Np * P, "out")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     ws = _workspace(lib.scd_fam_workspace_bytes(N, Np, L, P, prec), x.device, workspace)
-    o = make_opts(stream, prec, ws, y=y, conjugate=conjugate)
+    o = make_opts(stream, prec, ws, y=y, conjugate=conjugate, normalise=normalise)
     check(lib.scd_fam(_ptr(x), N, Np, L, P, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_fam")
     return out
 
 
 def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, workspace=None, schedule="auto",
-             y=None, conjugate=False):
+             y=None, conjugate=False, normalise=None):
     """SSCA estimate of the complex64 CUDA tensor x (N = x.numel()); returns complex64 [Np, N].
-    y: second signal of a cross estimate; conjugate: the conjugate estimate."""
+    y: second signal of a cross estimate; conjugate: the conjugate estimate; normalise: as
+    scd_fam."""
     torch = _torch()
     lib = load()
     _need(x, torch.complex64, 1, "x")
@@ -208,7 +215,7 @@ def scd_ssca(x, Np: int, window=None, out=None, precision="fp32", stream=None, w
     _need(out, torch.complex64, Np * N, "out")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     ws = _workspace(lib.scd_ssca_workspace_bytes(N, Np, prec), x.device, workspace)
-    o = make_opts(stream, prec, ws, schedule=schedule, y=y, conjugate=conjugate)
+    o = make_opts(stream, prec, ws, schedule=schedule, y=y, conjugate=conjugate, normalise=normalise)
     check(lib.scd_ssca(_ptr(x), N, Np, _ptr(window), _ptr(out), ctypes.byref(o)), "scd_ssca")
     return out
 

@@ -24,7 +24,7 @@ scd_status cuda_fail(cudaError_t e) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-const scd_opts kDefaultOpts = {nullptr, SCD_FP32, 1, nullptr, 0, nullptr, 0, SCD_SCHEDULE_AUTO, nullptr, 0};
+const scd_opts kDefaultOpts = {nullptr, SCD_FP32, 1, nullptr, 0, nullptr, 0, SCD_SCHEDULE_AUTO, nullptr, 0, 0};
 
 // Records opts.stage_events[i] (when the caller asked for at least `needed` events).
 struct StageMarks {
@@ -65,7 +65,8 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // The variant fields: y (when given) a complex64 device array aligned like x; conjugate 0 / 1.
 bool variant_ok(const scd_opts& o) {
-  return (!o.y || aligned(o.y, 8)) && (o.conjugate == 0 || o.conjugate == 1);
+  return (!o.y || aligned(o.y, 8)) && (o.conjugate == 0 || o.conjugate == 1) && o.normalise >= 0 &&
+         o.normalise <= 2;
 }
 
 }  // namespace
@@ -79,14 +80,16 @@ extern "C" {
 size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t P, int32_t precision) {
   (void)N; (void)L; (void)precision;
   if (Np < 1 || P < 1) return 0;
-  return 2 * round_up(sizeof(float) * 2 * (size_t)Np * (size_t)P, 256);   // X[kh][p], Y[lh][p]
+  // X[kh][p], Y[lh][p], then the input-normalisation area
+  return 2 * round_up(sizeof(float) * 2 * (size_t)Np * (size_t)P, 256) + scd::norm_workspace_bytes();
 }
 
 size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision) {
   (void)precision;
   if (Np < 1 || N < 1) return 0;
-  // the persistent schedule's X_g + rotating slots + counters cover the staged schedule's X_g
-  return scd::ssca_persistent_workspace(N, Np);
+  // the persistent schedule's X_g + rotating slots + counters cover the staged schedule's X_g;
+  // the input-normalisation area follows
+  return scd::ssca_persistent_workspace(N, Np) + scd::norm_workspace_bytes();
 }
 
 scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window, void* out,
@@ -101,11 +104,18 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
   if (scd::fault_host("fam")) return SCD_ERR_CUDA;
+  if (o.normalise && o.y) return SCD_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)o.stream;
   cudaError_t e;
   if (!window) {
     window = scd::table_hamming(Np, &e);
     if (!window) return cuda_fail(e);
+  }
+  if (o.normalise) {
+    void* area = (char*)o.workspace + need - scd::norm_workspace_bytes();
+    if ((e = scd::normalised_window((const float2*)x, (int64_t)(P - 1) * L + Np, window, Np, o.normalise, 1, area,
+                                    &window, st)) != cudaSuccess)
+      return cuda_fail(e);
   }
   float2* X = (float2*)o.workspace;
   const bool partner = o.y || o.conjugate;
@@ -143,11 +153,18 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   if (!o.workspace || o.workspace_bytes < need) return SCD_ERR_WORKSPACE;
   if (!aligned(o.workspace, 16)) return SCD_ERR_ARG;
   if (scd::fault_host("ssca")) return SCD_ERR_CUDA;
+  if (o.normalise && o.y) return SCD_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)o.stream;
   cudaError_t e;
   if (!window) {
     window = scd::table_hamming(Np, &e);
     if (!window) return cuda_fail(e);
+  }
+  if (o.normalise) {
+    void* area = (char*)o.workspace + need - scd::norm_workspace_bytes();
+    if ((e = scd::normalised_window((const float2*)x, N, window, Np, o.normalise, 2, area, &window, st)) !=
+        cudaSuccess)
+      return cuda_fail(e);
   }
   float2* ws = (float2*)o.workspace;
   scd::TuneEntry choice{o.schedule, 0, 0, 0.0};

@@ -86,6 +86,14 @@ scd_status ssca_persistent_tuned(const float2* x, const float2* y, bool conj, in
                                  float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision,
                                  int64_t item_bytes, int64_t slot_bytes);
 
+// ---------------------------------------------------------------- input normalisation (norm.cu)
+// Window a scaled for the input normalisation of the first n samples of x (mode 1: mean power
+// 1, mode 2: peak magnitude 1; `power` 1 for FAM, 2 for SSCA), written into `area`
+// (norm_workspace_bytes() bytes of device workspace); *window_out points into it.
+size_t norm_workspace_bytes();
+cudaError_t normalised_window(const float2* x, int64_t n, const float* a, int Np, int mode, int power, void* area,
+                              const float** window_out, cudaStream_t st);
+
 // ---------------------------------------------------------------- diagnostics (diag.cu)
 // Fault injection for tests, from the environment variable SCD_FAULT_INJECT (read on every
 // call, so a test can set and clear it):

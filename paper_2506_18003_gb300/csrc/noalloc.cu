@@ -81,7 +81,7 @@ scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t L, int3
     return SCD_ERR_UNSUPPORTED;
   }
   if (opts && opts->precision != SCD_FP32) return SCD_ERR_UNSUPPORTED;
-  if (opts && (opts->y || opts->conjugate)) return SCD_ERR_UNSUPPORTED;   // auto estimate only
+  if (opts && (opts->y || opts->conjugate || opts->normalise)) return SCD_ERR_UNSUPPORTED;   // plain auto estimate only
   cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
   float2* base = nullptr;
   cudaError_t e = scratch_address(&base);

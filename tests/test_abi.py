@@ -43,7 +43,7 @@ def test_status_strings(lib):
 
 
 def test_workspace_queries(lib):
-    assert lib.scd_fam_workspace_bytes(65728, 256, 64, 1024, 0) == 2 * 256 * 1024 * 8   # X and Y
+    assert lib.scd_fam_workspace_bytes(65728, 256, 64, 1024, 0) == 2 * 256 * 1024 * 8 + 2048   # X, Y, norm
     assert lib.scd_ssca_workspace_bytes(1 << 20, 256, 0) >= 256 * (1 << 20) * 8
     assert lib.scd_fam_workspace_bytes(280, 32, 8, 32, 0) % 256 == 0
 
@@ -188,3 +188,18 @@ def test_host_fault_injection(lib, monkeypatch):
     assert lib.scd_fam_map(FAKE, 32, 8, 32, FAKE, None) == binding.SCD_ERR_CUDA
     monkeypatch.delenv("SCD_FAULT_INJECT")
     assert lib.scd_fam_map(None, 32, 8, 32, FAKE, None) == binding.SCD_ERR_ARG
+
+
+def test_normalise_validation(lib):
+    o = binding.ScdOpts()
+    o.map_power = 1
+    o.workspace = 1 << 20
+    o.workspace_bytes = 1 << 40
+    o.normalise = 3
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_ARG
+    o.normalise = 1
+    o.y = 1 << 20                                        # cross estimate: not defined
+    assert lib.scd_fam(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_UNSUPPORTED
+    assert lib.scd_ssca(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_UNSUPPORTED
+    o.y = None
+    assert lib.scd_fam_noalloc(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_UNSUPPORTED

@@ -188,3 +188,30 @@ def test_profiles_equal_map_column_maxima_at_full_size(torch):
     assert torch.equal(prof, M.amax(dim=0))
     del S, M
     torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------------------- input normalisation
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+@pytest.mark.parametrize("normalise,mode", [("power", 1), ("peak", 2)])
+def test_fam_normalised_matches_oracle(torch, normalise, mode, precision):
+    Np, L, P = 32, 8, 64
+    N = (P - 1) * L + Np + 11                                 # the tail beyond the consumed samples
+    x = (signals.modulated("qpsk", N, 4, 0.08, 6.0, seed=6600) * np.complex64(7.5)).astype(np.complex64)
+    a = orc.hamming_window(Np)
+    ref = orc.fam(x, a, Np, L, P, normalise=mode)
+    got = binding.scd_fam(_dev(torch, x), Np, L, P, window=_dev(torch, a), precision=precision,
+                          normalise=normalise).cpu().numpy()
+    assert _rel(got, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("schedule", ["stages", "persistent"])
+@pytest.mark.parametrize("normalise,mode", [("power", 1), ("peak", 2)])
+def test_ssca_normalised_matches_oracle(torch, normalise, mode, schedule):
+    N, Np = 1 << 13, 64
+    x = (signals.modulated("bpsk", N, 8, -0.05, 6.0, seed=6700, pulse="rect") * np.complex64(0.03)).astype(np.complex64)
+    a = orc.hamming_window(Np)
+    ref = orc.ssca(x, a, Np, normalise=mode)
+    got = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a), schedule=schedule,
+                           normalise=normalise).cpu().numpy()
+    binding.scd_check_device()
+    assert _rel(got, ref) <= TOL["fp32"]
