@@ -18,6 +18,9 @@ Conventions (fs = 1; all axes stored "fftshifted"):
     down-conversion phase being Np-periodic in k);
   * FAM second-FFT bin q in [-P/2, P/2) is stored at qh = q + P/2;
   * SSCA bin q in [-N/2, N/2) is stored at sh = q + N/2;
+  * P and N need not be powers of two; for an odd size M the signed bins are
+    q in [-(M-1)/2, (M-1)/2], stored at q + floor(M/2) (the order numpy's fftshift gives:
+    the zero bin at floor(M/2), the most negative bin first);
   * W_M^j = exp(-i*2*pi*j/M); every phase index is an exact integer product reduced
     to its non-negative residue mod M before it becomes an angle;
   * windows g, g_d of the SCD low-pass (Sec. II-A, II-B, II-C) are rectangular (= 1);
@@ -28,7 +31,7 @@ Besides the auto estimate (the paper's case) both estimators take a second signa
 product without the conjugation); alpha profiles are the column maxima of the maps.
 
 Pins (tests/test_oracle_*.py): brute-force triple sums on tiny inputs (auto, cross and
-conjugate), direct vs fft mode, cross Hermitian symmetry, the conjugate estimate as a
+conjugate; power-of-two and other sizes, odd ones included), direct vs fft mode, cross Hermitian symmetry, the conjugate estimate as a
 cross estimate against conj(y) with the l axis reversed, the averaged-periodogram identity at alpha = 0 (also against scipy's Welch
 estimate), the lag-windowed correlogram at alpha = 0 for SSCA, exact conjugate
 symmetry (FAM), exact channel-shift invariance, |c|^2 scaling, the closed-form FAM
@@ -178,10 +181,16 @@ def fam_demodulates(x, a, Np: int, L: int, P: int, mode: str = "fft", scale: flo
     return (spectra * down).T.copy()                              # [kh][p]
 
 
+def _signed_bins(M: int) -> np.ndarray:
+    """Signed bins of a size-M DFT in stored order: q in [-floor(M/2), M - floor(M/2)),
+    q stored at q + floor(M/2) (for even M, [-M/2, M/2))."""
+    return np.arange(-(M // 2), M - M // 2, dtype=np.int64)
+
+
 def _fam_second_fft(z: np.ndarray, P: int, mode: str) -> np.ndarray:
-    """S(q) = sum_{p<P} z(p) W_P^{(q p) mod P} for q in [-P/2, P/2), stored at q + P/2."""
-    q = np.arange(-P // 2, P // 2, dtype=np.int64)
-    return _dft_rows(z, P, q, mode)
+    """S(q) = sum_{p<P} z(p) W_P^{(q p) mod P} for the signed bins q of _signed_bins(P),
+    stored at q + floor(P/2)."""
+    return _dft_rows(z, P, _signed_bins(P), mode)
 
 
 def fam_pairs(x, a, Np: int, L: int, P: int, kh, lh, mode: str = "fft", y=None,
@@ -263,9 +272,10 @@ def ssca_cdp(x, a, Np: int, n, channels=None, mode: str = "fft", y=None,
 
 def ssca_strip(Xg_row: np.ndarray, mode: str = "fft") -> np.ndarray:
     """N-point strip transform of one channel (Eq. II.B-SSCA_auto, time origin at the first
-    sample): S(q) = sum_{n<N} X_g(n) W_N^{(q n) mod N}, q in [-N/2, N/2) stored at q + N/2."""
+    sample): S(q) = sum_{n<N} X_g(n) W_N^{(q n) mod N}, q in [-N/2, N/2) stored at q + N/2
+    (any N: the signed bins of _signed_bins(N))."""
     N = Xg_row.shape[-1]
-    q = np.arange(-N // 2, N // 2, dtype=np.int64)
+    q = _signed_bins(N)
     if mode == "direct":
         if N > 4096:
             raise ValueError("direct SSCA strip DFT is limited to N <= 4096")
@@ -346,8 +356,11 @@ def ssca_map_coords(N: int, Np: int):
 
     ah = k N/Np + q + N             (alpha = (ah - N)/N, in [-1, 1))
     fh = floor((k N/Np - q + N) / (2 N/Np))   (f in [fh, fh+1) * 1/Np - 1/2)
-    Returns int64 arrays kh, sh, fh, ah for all Np*N cells.
+    The channel centres k/Np fall on the alpha grid 1/N only when Np divides N, so the map
+    needs that.  Returns int64 arrays kh, sh, fh, ah for all Np*N cells.
     """
+    if N % Np:
+        raise ValueError("SSCA map needs Np to divide N")
     k = _signed_channels(Np)
     q = np.arange(-N // 2, N // 2, dtype=np.int64)
     kk, qq = np.meshgrid(k, q, indexing="ij")

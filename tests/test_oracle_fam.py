@@ -45,7 +45,7 @@ def _bruteforce_fam(x, a, Np, L, P):
     return out
 
 
-@pytest.mark.parametrize("Np,L,P", [(4, 1, 8), (8, 2, 16)])
+@pytest.mark.parametrize("Np,L,P", [(4, 1, 8), (8, 2, 16), (4, 1, 5), (4, 2, 6), (8, 2, 7)])
 def test_fam_bruteforce_tiny(Np, L, P):
     N = (P - 1) * L + Np
     x = signals.awgn(N, seed=11 + Np)
@@ -55,7 +55,7 @@ def test_fam_bruteforce_tiny(Np, L, P):
         assert _rel(orc.fam(x, a, Np, L, P, mode=mode), ref) < 1e-12
 
 
-@pytest.mark.parametrize("Np,L,P", [(16, 4, 32), (32, 8, 64), (64, 16, 16)])
+@pytest.mark.parametrize("Np,L,P", [(16, 4, 32), (32, 8, 64), (64, 16, 16), (16, 4, 33), (32, 8, 100)])
 def test_fam_direct_matches_fft(Np, L, P):
     N = (P - 1) * L + Np + 5
     x = signals.modulated("qpsk", N, 4, 0.07, 10.0, seed=3)
@@ -88,11 +88,13 @@ def test_fam_alpha0_is_averaged_periodogram():
     assert _rel(diag.real, pgram[np.mod(k, Np)]) < 1e-13
 
 
-def test_fam_alpha0_matches_scipy_welch():
+@pytest.mark.parametrize("P", [64, 50, 45])
+def test_fam_alpha0_matches_scipy_welch(P):
     """Welch's PSD estimate (scipy) with the same window, segment length Np, hop L and
-    P segments, scaled back to a raw sum: S(k,k,0) = welch * P * sum(a^2)."""
+    P segments, scaled back to a raw sum: S(k,k,0) = welch * P * sum(a^2).  The zero bin
+    is stored at floor(P/2) for any P."""
     signal = pytest.importorskip("scipy.signal")
-    Np, L, P = 64, 16, 64
+    Np, L = 64, 16
     N = (P - 1) * L + Np
     x = signals.modulated("bpsk", N, 8, 0.05, 10.0, seed=5, pulse="rect")
     a = orc.hamming_window(Np)
@@ -105,13 +107,16 @@ def test_fam_alpha0_matches_scipy_welch():
     assert _rel(diag, ref[np.mod(k, Np)]) < 1e-12
 
 
-def test_fam_conjugate_symmetry_exact():
-    """S(l, k, -q) = conj(S(k, l, q)): swapping the pair conjugates z(p)."""
-    Np, L, P = 32, 8, 32
-    x = signals.fam_small_bpsk()["x"]
+@pytest.mark.parametrize("P", [32, 31, 24])
+def test_fam_conjugate_symmetry_exact(P):
+    """S(l, k, -q) = conj(S(k, l, q)): swapping the pair conjugates z(p).  Bin q is stored
+    at q + floor(P/2), so -q sits at 2 floor(P/2) - qh (mod P): P - qh for even P and
+    P - 1 - qh for odd P, which pins where the zero bin of an odd size is stored."""
+    Np, L = 32, 8
+    x = signals.awgn((P - 1) * L + Np, seed=40 + P)
     S = orc.fam(x, orc.hamming_window(Np), Np, L, P)
     qh = np.arange(P)
-    flipped = S.transpose(1, 0, 2)[:, :, np.mod(P - qh, P)]
+    flipped = S.transpose(1, 0, 2)[:, :, np.mod(2 * (P // 2) - qh, P)]
     assert _rel(flipped, np.conj(S)) < 1e-14
 
 
@@ -141,7 +146,7 @@ def test_fam_scaling():
     assert _rel(S2, abs(complex(c)) ** 2 * S) < 1e-6
 
 
-@pytest.mark.parametrize("Np,L,P", [(16, 4, 16), (32, 8, 32), (16, 2, 64)])
+@pytest.mark.parametrize("Np,L,P", [(16, 4, 16), (32, 8, 32), (16, 2, 64), (16, 4, 12), (16, 16, 9)])
 def test_fam_tones_closed_form(Np, L, P):
     """Closed form for x = sum_i A_i exp(i 2 pi c_i n / Np) (channel-centred tones):
     X(p,k) = sum_i A_i W_Np^{(k - c_i) p L} Ahat(k - c_i), Ahat(m) = sum_n a[n] W_Np^{m n},
@@ -166,7 +171,7 @@ def test_fam_tones_closed_form(Np, L, P):
                 for cj, Aj in zip(cs, amps):
                     m = ((k - ci) - (l - cj)) * P * L // Np
                     q = (-m) % P                       # q = -m (mod P), in natural order
-                    qs = q - P if q >= P // 2 else q   # signed
+                    qs = q - P if q >= P - P // 2 else q   # signed: [-floor(P/2), P - floor(P/2))
                     ref[kh, lh, qs + P // 2] += P * Ai * np.conj(Aj) * ahat(k - ci) * np.conj(ahat(l - cj))
     S = orc.fam(x, orc.hamming_window(Np), Np, L, P)
     assert _rel(S, ref) < 2e-6                          # complex64 rounding of the tones

@@ -15,7 +15,7 @@ from paper_2506_18003_gb300 import signals
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")
 
 
-@pytest.mark.parametrize("Np,L,P", [(16, 4, 16), (32, 8, 32), (16, 2, 64), (64, 16, 128)])
+@pytest.mark.parametrize("Np,L,P", [(16, 4, 16), (32, 8, 32), (16, 2, 64), (64, 16, 128), (16, 4, 12), (64, 16, 100)])
 def test_fam_map_is_injective_and_inside_grid(Np, L, P):
     kh, lh, qh, fh, ah = orc.fam_map_coords(Np, L, P)
     Q = P * L // Np
@@ -39,7 +39,7 @@ def test_fam_map_is_injective_and_inside_grid(Np, L, P):
     assert np.all(np.abs(f) + np.abs(alpha) / 2 <= 0.5 + 0.5 / Np + 1e-12)
 
 
-@pytest.mark.parametrize("N,Np", [(64, 16), (4096, 32), (1 << 12, 256)])
+@pytest.mark.parametrize("N,Np", [(64, 16), (4096, 32), (1 << 12, 256), (3 * 1024, 32), (48, 16)])
 def test_ssca_map_is_injective_and_inside_grid(N, Np):
     kh, sh, fh, ah = orc.ssca_map_coords(N, Np)
     assert fh.min() >= 0 and fh.max() < Np and ah.min() >= 0 and ah.max() < 2 * N

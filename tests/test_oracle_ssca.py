@@ -39,7 +39,7 @@ def _bruteforce_ssca(x, a, Np):
     return out
 
 
-@pytest.mark.parametrize("N,Np", [(16, 4), (32, 8), (64, 16)])
+@pytest.mark.parametrize("N,Np", [(16, 4), (32, 8), (64, 16), (15, 4), (24, 8), (33, 16)])
 def test_ssca_bruteforce_tiny(N, Np):
     x = signals.awgn(N, seed=100 + N)
     a = orc.hamming_window(Np)
@@ -48,7 +48,7 @@ def test_ssca_bruteforce_tiny(N, Np):
         assert _rel(orc.ssca(x, a, Np, mode=mode), ref) < 1e-12
 
 
-@pytest.mark.parametrize("N,Np", [(1024, 16), (4096, 32), (2048, 256)])
+@pytest.mark.parametrize("N,Np", [(1024, 16), (4096, 32), (2048, 256), (1000, 16), (3001, 64)])
 def test_ssca_direct_matches_fft(N, Np):
     x = signals.modulated("qpsk", N, 4, 0.1, 5.0, seed=7)
     a = orc.hamming_window(Np)
@@ -64,7 +64,7 @@ def test_ssca_channel_subset_matches_full():
     assert _rel(orc.ssca(x, a, Np, channels=ch, chunk=1000), full[ch]) < 1e-14
 
 
-@pytest.mark.parametrize("N,Np", [(512, 16), (2048, 64)])
+@pytest.mark.parametrize("N,Np", [(512, 16), (2048, 64), (1008, 16), (3 * 1024, 64)])
 def test_ssca_alpha0_is_lag_windowed_correlogram(N, Np):
     """At q = -k N/Np (alpha = 0, f = k/Np):
     S = sum_{tau=-Np/2}^{Np/2-1} a[tau + Np/2] R(tau) W_Np^{k tau},
@@ -105,13 +105,14 @@ def test_ssca_scaling():
     assert _rel(orc.ssca((x * c).astype(np.complex64), a, Np), abs(complex(c)) ** 2 * orc.ssca(x, a, Np)) < 1e-6
 
 
-def test_ssca_two_tones_feature_location():
+@pytest.mark.parametrize("N", [4096, 3200])
+def test_ssca_two_tones_feature_location(N):
     """Two channel-centred tones A1 exp(i 2 pi f1 n) + A2 exp(i 2 pi f2 n): channel f1
     times conj(x) carries A1 conj(A2) exp(-i 2 pi f2 n), so the cell k = f1 Np,
     q = -f2 N (alpha = f1 - f2, f = (f1 + f2)/2) holds about N A1 conj(A2) sum(a).
     The phase pins which factor is conjugated (the sign convention of alpha), and the
     map puts the peak at that (f, alpha)."""
-    N, Np = 4096, 32
+    Np = 32
     c1, c2 = 5, -3
     f1, f2 = c1 / Np, c2 / Np
     A1, A2 = 1.0, np.exp(1j * 0.7)
@@ -151,3 +152,19 @@ def test_ssca_white_noise_floor():
     on = np.mean([S[kh, (N // 2 - (kh - Np // 2) * (N // Np)) % N] for kh in range(Np)])
     off = np.mean(S)
     assert off / on < 3.0 / math.sqrt(N / Np)
+
+
+def test_ssca_odd_length_zero_bin():
+    """A constant input: channel k = 0 sees X_T(n, 0) = sum(a) away from the edges, so
+    X_g(n, 0) is constant there and its strip transform peaks in the zero bin q = 0,
+    stored at floor(N/2) for an odd N as well (a wrong centre would move the peak)."""
+    N, Np = 2049, 16
+    x = signals.tones(N, [0.0], [1.0])
+    S = np.abs(orc.ssca(x, orc.hamming_window(Np), Np))
+    assert int(np.argmax(S[Np // 2])) == N // 2
+    assert S[Np // 2, N // 2] > 50 * np.median(S[Np // 2])
+
+
+def test_ssca_map_needs_np_to_divide_n():
+    with pytest.raises(ValueError):
+        orc.ssca_map_coords(3000, 64)
