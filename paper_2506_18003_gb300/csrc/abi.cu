@@ -40,13 +40,18 @@ const scd_opts& opts_or_default(const scd_opts* o) { return o ? *o : kDefaultOpt
 
 bool np_ok(int32_t Np) { return Np >= 16 && Np <= 256 && scd::is_pow2(Np); }
 
+// Sizes that are not powers of two run on Bluestein's identity with transforms of size
+// M >= 2n - 1: FAM pairs in one CTA (M <= 16384), SSCA four-step transforms (M <= 2^20).
+constexpr int32_t kMaxAnyP = 8192;
+constexpr int64_t kMaxAnyN = int64_t(1) << 19;
+
 scd_status check_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window,
                      const void* out) {
   if (!x || !out) return SCD_ERR_ARG;
   if (!aligned(x, 8) || !aligned(out, 16) || (window && !aligned(window, 4))) return SCD_ERR_ARG;
   if (L < 1 || Np < 1 || P < 1 || N < 1) return SCD_ERR_ARG;
   if (!np_ok(Np)) return SCD_ERR_UNSUPPORTED;
-  if (P < 2 || P > 16384 || !scd::is_pow2(P)) return SCD_ERR_UNSUPPORTED;
+  if (P < 2 || P > 16384 || (!scd::is_pow2(P) && P > kMaxAnyP)) return SCD_ERR_UNSUPPORTED;
   if ((int64_t)(P - 1) * L + Np > N) return SCD_ERR_ARG;
   if ((int64_t)(P - 1) * L + Np > (int64_t(1) << 31)) return SCD_ERR_UNSUPPORTED;
   return SCD_OK;
@@ -57,7 +62,7 @@ scd_status check_ssca(const void* x, int64_t N, int32_t Np, const float* window,
   if (!aligned(x, 8) || !aligned(out, 16) || (window && !aligned(window, 4))) return SCD_ERR_ARG;
   if (N < 1 || Np < 1) return SCD_ERR_ARG;
   if (!np_ok(Np)) return SCD_ERR_UNSUPPORTED;
-  if (N < 4096 || N > (1 << 20) || !scd::is_pow2(N)) return SCD_ERR_UNSUPPORTED;
+  if (N < 4096 || N > (1 << 20) || (!scd::is_pow2(N) && N > kMaxAnyN)) return SCD_ERR_UNSUPPORTED;
   return SCD_OK;
 }
 
@@ -87,6 +92,7 @@ size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t P, int3
 size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision) {
   (void)precision;
   if (Np < 1 || N < 1) return 0;
+  if (!scd::is_pow2(N)) return scd::ssca_any_workspace(N, Np) + scd::norm_workspace_bytes();
   // the persistent schedule's X_g + rotating slots + counters cover the staged schedule's X_g;
   // the input-normalisation area follows
   return scd::ssca_persistent_workspace(N, Np) + scd::norm_workspace_bytes();
@@ -135,7 +141,9 @@ scd_status scd_fam(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, c
     Y = Z;
   }
   if ((e = m.mark(mk++, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = scd::fam_pair_fft(X, Y, Np, P, (float2*)out, st, o.precision)) != cudaSuccess) return cuda_fail(e);
+  e = scd::is_pow2(P) ? scd::fam_pair_fft(X, Y, Np, P, (float2*)out, st, o.precision)
+                      : scd::fam_pair_fft_any(X, Y, Np, P, (float2*)out, st, o.precision);
+  if (e != cudaSuccess) return cuda_fail(e);
   if ((e = m.mark(mk++, st)) != cudaSuccess) return cuda_fail(e);
   return SCD_OK;
 }
@@ -167,6 +175,21 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
       return cuda_fail(e);
   }
   float2* ws = (float2*)o.workspace;
+  if (!scd::is_pow2(N)) {
+    // any N: the strip transform on Bluestein's identity (staged kernels only)
+    if (o.schedule == SCD_SCHEDULE_PERSISTENT) return SCD_ERR_UNSUPPORTED;
+    if (o.schedule != SCD_SCHEDULE_AUTO && o.schedule != SCD_SCHEDULE_STAGES) return SCD_ERR_ARG;
+    StageMarks m{o, 4};
+    if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = scd::ssca_any_cdp((const float2*)x, y, conj, N, Np, window, ws, st, o.precision)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = scd::ssca_any_first(N, Np, ws, st, o.precision)) != cudaSuccess) return cuda_fail(e);
+    if ((e = m.mark(2, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = scd::ssca_any_second(N, Np, ws, (float2*)out, st, o.precision)) != cudaSuccess) return cuda_fail(e);
+    if ((e = m.mark(3, st)) != cudaSuccess) return cuda_fail(e);
+    return SCD_OK;
+  }
   scd::TuneEntry choice{o.schedule, 0, 0, 0.0};
   if (o.schedule == SCD_SCHEDULE_AUTO) choice = scd::ssca_auto_choice(N, Np, o.precision);
   if (choice.schedule != SCD_SCHEDULE_STAGES && choice.schedule != SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
@@ -281,17 +304,22 @@ scd_status scd_prepare(int32_t estimator, int64_t N, int32_t Np, int32_t P) {
   cudaError_t e;
   if (!scd::table_hamming(Np, &e) || !scd::table_roots(Np, &e) || !scd::table_pass(Np, &e)) return cuda_fail(e);
   if (estimator == 0) {
-    if (P < 2 || P > 16384 || !scd::is_pow2(P)) return SCD_ERR_UNSUPPORTED;
-    if (!scd::table_pass(P, &e)) return cuda_fail(e);
+    if (P < 2 || P > 16384 || (!scd::is_pow2(P) && P > kMaxAnyP)) return SCD_ERR_UNSUPPORTED;
+    if (scd::is_pow2(P)) return scd::table_pass(P, &e) ? SCD_OK : cuda_fail(e);
+    const int64_t M = scd::bluestein_len_host(P);
+    if (!scd::table_pass((int)M, &e) || !scd::table_chirp(P, &e) || !scd::table_bluestein(P, M, &e))
+      return cuda_fail(e);
     return SCD_OK;
   }
   if (estimator == 1) {
-    if (N < 4096 || N > (1 << 20) || !scd::is_pow2(N)) return SCD_ERR_UNSUPPORTED;
+    if (N < 4096 || N > (1 << 20) || (!scd::is_pow2(N) && N > kMaxAnyN)) return SCD_ERR_UNSUPPORTED;
+    const int64_t M = scd::is_pow2(N) ? N : scd::bluestein_len_host(N);
     int M1, M2;
-    scd::ssca_split(N, &M1, &M2);
-    if (!scd::table_roots((int)N, &e) || !scd::table_pass(M1, &e) || !scd::table_pass(M2, &e) ||
-        !scd::table_cols((int)N, M1, scd::ssca_cols_per_tile(M1), &e))
+    scd::ssca_split(M, &M1, &M2);
+    if (!scd::table_roots((int)M, &e) || !scd::table_pass(M1, &e) || !scd::table_pass(M2, &e) ||
+        !scd::table_cols((int)M, M1, scd::ssca_cols_per_tile(M1), &e))
       return cuda_fail(e);
+    if (!scd::is_pow2(N) && (!scd::table_chirp(N, &e) || !scd::table_bluestein(N, M, &e))) return cuda_fail(e);
     return SCD_OK;
   }
   return SCD_ERR_ARG;

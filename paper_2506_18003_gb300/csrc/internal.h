@@ -19,6 +19,10 @@ const float2* table_roots(int M, cudaError_t* err);        // W_M^j, j in [0, M)
 const float2* table_pass(int M, cudaError_t* err);         // Stockham pass twiddles of a size-M FFT
 const float2* table_cols(int N, int M1, int C, cudaError_t* err);  // W_N^{c m1'}, [m1'][c], c < C
 const float* table_hamming(int Np, cudaError_t* err);      // default window, float32
+// Bluestein tables of a length-N DFT carried by size-M transforms (M a power of two >= 2N - 1):
+// chirp c[j] = W_{2N}^{(j^2) mod 2N} (j < N) and Bh = FFT_M(bt) / M (bluestein.cuh)
+const float2* table_chirp(int64_t N, cudaError_t* err);
+const float2* table_bluestein(int64_t N, int64_t M, cudaError_t* err);
 // bf16 hi/lo complex-as-real DFT matrices of the radices of a size-M plan (tensor-core form)
 const unsigned char* table_tc_bmats(int M, int* bytes, cudaError_t* err);
 // one word per device, set by kernels whose bounded device-side waits expired
@@ -61,6 +65,22 @@ size_t ssca_persistent_workspace(int64_t N, int Np);
 scd_status ssca_persistent(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
                            float2* out, void* ws, size_t ws_bytes, cudaStream_t st, int precision);
 void release_single_plans();
+
+// ---------------------------------------------------------------- any-length DFTs (bluestein.cu)
+// FAM pair stage for a P that is not a power of two (3 <= P <= 8192), same contract as
+// fam_pair_fft.
+cudaError_t fam_pair_fft_any(const float2* X, const float2* Y, int Np, int P, float2* out, cudaStream_t st,
+                             int precision);
+// SSCA for an N that is not a power of two (4096 <= N <= 2^19): the strip transform of length N
+// as Bluestein's cyclic convolution of length M = bluestein_len(N), in three stages on the
+// workspace ws (ssca_any_workspace bytes): channeliser + CDP with the chirp folded into the
+// second factor; the first size-M transform times the kernel spectrum; the second transform
+// into the fftshifted output.
+size_t ssca_any_workspace(int64_t N, int Np);
+cudaError_t ssca_any_cdp(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
+                         void* ws, cudaStream_t st, int precision);
+cudaError_t ssca_any_first(int64_t N, int Np, void* ws, cudaStream_t st, int precision);
+cudaError_t ssca_any_second(int64_t N, int Np, void* ws, float2* out, cudaStream_t st, int precision);
 
 // ---------------------------------------------------------------- maps (map.cu)
 cudaError_t fam_map(const float2* S, int Np, int L, int P, int power, bool conj, float* map, cudaStream_t st);
@@ -119,5 +139,7 @@ void set_last_error(const char* msg);
 // ---------------------------------------------------------------- helpers
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 inline int ilog2(int64_t v) { int r = 0; while ((int64_t(1) << r) < v) ++r; return r; }
+// smallest power of two >= 2n - 1 (the cyclic length of a length-n Bluestein DFT)
+inline int64_t bluestein_len_host(int64_t n) { int64_t m = 1; while (m < 2 * n - 1) m <<= 1; return m; }
 
 }  // namespace scd

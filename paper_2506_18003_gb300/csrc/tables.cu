@@ -1,5 +1,8 @@
 // K0: FP64 phase and twiddle tables.
 //
+// Also the two tables of the any-length DFTs (bluestein.cuh): the chirp W_{2N}^{j^2} and the
+// spectrum of its conjugate, computed with an FP64 radix-2 FFT and rounded to float once.
+//
 // The rotate factor W_N^{(m2 m1') mod N} of the decomposed FFT (Eq. Chap4_2DFFT) and the
 // Stockham pass twiddles are all of the form W_M^j with an exact integer j in [0, M) (the
 // channelisers' down-conversion phases need no table: they are folded into the FFT's input
@@ -104,6 +107,46 @@ __global__ void __launch_bounds__(256) k_chebwin(float* out, int Np, double atte
   if (n < Np) out[n] = (float)(v / red[0]);
 }
 
+// Chirp of Bluestein's identity for a length-N DFT: c[j] = W_{2N}^{(j^2) mod 2N}, j < N (the
+// exponent reduced exactly in 64-bit integers before it becomes an angle).
+__global__ void k_chirp(float2* out, int64_t N) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = root_fp64((j * j) % (2 * N), 2 * N);
+}
+
+// bt[j] = conj(c[j]) for j < N, conj(c[M - j]) for M - j < N, 0 between (FP64).
+__global__ void k_bluestein_kernel(double2* bt, int64_t N, int64_t M) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = j < N ? j : (M - j < N ? M - j : -1);
+    double s = 0.0, c = 0.0;
+    if (i >= 0) sincospi((double)((i * i) % (2 * N)) / (double)N, &s, &c);
+    bt[j] = i >= 0 ? make_double2(c, s) : make_double2(0.0, 0.0);       // conj(W_{2N}^{i^2})
+  }
+}
+
+// One radix-2 pass of an FP64 Stockham FFT of size M (the recurrence of fft.cuh with R = 2):
+// for s < M/(2p), k < p:  a = in[k + s p], b = in[k + (s + M/(2p)) p] W_{2p}^k,
+// out[k + 2 s p] = a + b, out[k + p + 2 s p] = a - b.  After the pass with p = M/2 the output is
+// the transform in natural order.
+__global__ void k_fft64_pass(const double2* __restrict__ in, double2* __restrict__ out, int64_t M, int64_t p) {
+  const int64_t half = M / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < half; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / p, k = e % p;
+    double sn, cs;
+    sincospi((double)k / (double)p, &sn, &cs);
+    const double2 a = in[k + s * p], bi = in[k + (s + half / p) * p];
+    const double2 b = make_double2(bi.x * cs + bi.y * sn, bi.y * cs - bi.x * sn);   // bi W_{2p}^k
+    out[k + 2 * s * p] = make_double2(a.x + b.x, a.y + b.y);
+    out[k + p + 2 * s * p] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+
+__global__ void k_scale_round(const double2* __restrict__ in, float2* __restrict__ out, int64_t M) {
+  const double inv = 1.0 / (double)M;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = make_float2((float)(in[j].x * inv), (float)(in[j].y * inv));
+}
+
 struct Key {
   int dev, kind;
   int64_t a, b, c;
@@ -175,6 +218,29 @@ const float2* table_pass(int M, cudaError_t* err) {
 const float2* table_cols(int N, int M1, int C, cudaError_t* err) {
   return (const float2*)get_or_build(2, N, M1, C, sizeof(float2) * (size_t)M1 * C, err, [&](void* p, cudaStream_t st) {
     k_cols<<<grid_for((int64_t)M1 * C), 256, 0, st>>>((float2*)p, N, M1, C);
+  });
+}
+
+const float2* table_chirp(int64_t N, cudaError_t* err) {
+  return (const float2*)get_or_build(8, N, 0, 0, sizeof(float2) * (size_t)N, err, [&](void* p, cudaStream_t st) {
+    k_chirp<<<grid_for(N), 256, 0, st>>>((float2*)p, N);
+  });
+}
+
+const float2* table_bluestein(int64_t N, int64_t M, cudaError_t* err) {
+  if (M < 2 * N - 1 || !is_pow2(M)) { *err = cudaErrorInvalidValue; return nullptr; }
+  return (const float2*)get_or_build(9, N, M, 0, sizeof(float2) * (size_t)M, err, [&](void* p, cudaStream_t st) {
+    double2* buf = nullptr;
+    if (cudaMallocAsync((void**)&buf, sizeof(double2) * 2 * (size_t)M, st) != cudaSuccess) return;
+    double2* a = buf;
+    double2* b = buf + M;
+    k_bluestein_kernel<<<grid_for(M), 256, 0, st>>>(a, N, M);
+    for (int64_t q = 1; q < M; q <<= 1) {
+      k_fft64_pass<<<grid_for(M / 2), 256, 0, st>>>(a, b, M, q);
+      double2* t = a; a = b; b = t;
+    }
+    k_scale_round<<<grid_for(M), 256, 0, st>>>(a, (float2*)p, M);
+    cudaFreeAsync(buf, st);
   });
 }
 

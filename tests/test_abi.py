@@ -46,6 +46,8 @@ def test_workspace_queries(lib):
     assert lib.scd_fam_workspace_bytes(65728, 256, 64, 1024, 0) == 2 * 256 * 1024 * 8 + 2048   # X, Y, norm
     assert lib.scd_ssca_workspace_bytes(1 << 20, 256, 0) >= 256 * (1 << 20) * 8
     assert lib.scd_fam_workspace_bytes(280, 32, 8, 32, 0) % 256 == 0
+    # a length that is not a power of two: two channel rows of the 2^14-point cyclic transform
+    assert lib.scd_ssca_workspace_bytes(5000, 32, 0) >= 2 * 32 * (1 << 14) * 8
 
 
 FAKE = ctypes.c_void_p(1 << 20)        # aligned, never dereferenced: validation fails first
@@ -58,7 +60,8 @@ FAKE = ctypes.c_void_p(1 << 20)        # aligned, never dereferenced: validation
     (280, 24, 8, 32, binding.SCD_ERR_UNSUPPORTED),     # Np not a power of two
     (280, 8, 8, 32, binding.SCD_ERR_UNSUPPORTED),      # Np below 16
     (4000, 512, 8, 32, binding.SCD_ERR_UNSUPPORTED),   # Np above 256
-    (280, 32, 8, 30, binding.SCD_ERR_UNSUPPORTED),     # P not a power of two
+    (280, 32, 8, 30, binding.SCD_ERR_WORKSPACE),       # P not a power of two: accepted (no workspace given)
+    (1 << 20, 32, 1, 8193, binding.SCD_ERR_UNSUPPORTED),   # above 8192 and not a power of two
     (1 << 20, 32, 1, 32768, binding.SCD_ERR_UNSUPPORTED),
 ])
 def test_fam_argument_validation(lib, N, Np, L, P, expect):
@@ -80,7 +83,9 @@ def test_null_and_misaligned_pointers(lib):
 @pytest.mark.parametrize("N,Np,expect", [
     (2048, 32, binding.SCD_ERR_UNSUPPORTED),           # below 2^12
     (1 << 21, 32, binding.SCD_ERR_UNSUPPORTED),        # above 2^20
-    (5000, 32, binding.SCD_ERR_UNSUPPORTED),           # not a power of two
+    (5000, 32, binding.SCD_ERR_WORKSPACE),             # not a power of two: accepted (no workspace given)
+    (4095, 32, binding.SCD_ERR_UNSUPPORTED),           # below 2^12
+    ((1 << 19) + 1, 32, binding.SCD_ERR_UNSUPPORTED),  # above 2^19 and not a power of two
     (4096, 48, binding.SCD_ERR_UNSUPPORTED),
 ])
 def test_ssca_argument_validation(lib, N, Np, expect):
