@@ -590,9 +590,13 @@ def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
     pf = torch.empty(2 * P * L, dtype=torch.float32, device=dev)
     ps = torch.empty(2 * Ns, dtype=torch.float32, device=dev)
     lib = binding.load()
-    work = torch.empty(max(lib.scd_fam_workspace_bytes(Nf, Np, L, P, 0), lib.scd_ssca_workspace_bytes(Ns, Nps, 0)),
+    # lengths that are not powers of two (Bluestein's identity): FAM P = 1000, SSCA N = 500,000
+    Pa, Na = 1000, 500000
+    work = torch.empty(max(lib.scd_fam_workspace_bytes(Nf, Np, L, P, 0), lib.scd_ssca_workspace_bytes(Ns, Nps, 0),
+                           lib.scd_fam_workspace_bytes(Nf, Np, L, Pa, 0), lib.scd_ssca_workspace_bytes(Na, Nps, 0)),
                        dtype=torch.uint8, device=dev)
     used = (P - 1) * L + Np
+    used_a = (Pa - 1) * L + Np
     cases = {
         "fam_cross": (lambda: binding.scd_fam(xf, Np, L, P, out=Sf, stream=stream, workspace=work, y=yf),
                       16 * used + 8 * Np * Np * P),
@@ -606,6 +610,12 @@ def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
                            8 * Ns + 8 * Nps * Ns),
         "ssca_alpha_profile": (lambda: binding.scd_ssca_alpha_profile(Ss, Ns, Nps, ps, stream=stream),
                                8 * Nps * Ns + 4 * 2 * Ns),
+        "fam_any_p1000": (lambda: binding.scd_fam(xf[:used_a], Np, L, Pa, out=Sf.view(-1)[:Np * Np * Pa],
+                                                  stream=stream, workspace=work),
+                          8 * used_a + 8 * Np * Np * Pa),
+        "ssca_any_n500000": (lambda: binding.scd_ssca(xs[:Na], Nps, out=Ss.view(-1)[:Nps * Na], stream=stream,
+                                                      workspace=work),
+                             8 * Na + 8 * Nps * Na),
     }
     out = {}
     with torch.cuda.stream(stream):
@@ -624,7 +634,8 @@ def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
     binding.scd_check_device(stream)
     del Sf, Ss, work
     torch.cuda.empty_cache()
-    out["sizes"] = "FAM N=65728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256; FP32 form; %d calls each" % reps
+    out["sizes"] = ("FAM N=65728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256; any-length: FAM P=1000 (N=64,192), "
+                    "SSCA N=500,000 (Bluestein, cyclic length 2^20); FP32 form; %d calls each" % reps)
     # streaming: one group of windows per step, new samples copied in from pinned host memory
     # every step (scd_stream_advance) and the plan's graph replayed (scd_batch_run)
     for name, est, W, hop, nwin, Npw, Lw in (("ssca_stream", "ssca", 1 << 16, 1 << 15, 16, 256, 1),

@@ -12,11 +12,11 @@
 //   0. the inputs padded with zeros to a multiple of the channeliser tile and the chirp folded
 //      into the second factor (k_bl_prep), then the power-of-two K3 (channeliser + CDP):
 //      X_g(n, k) c[n] for n < N, zero beyond, rows of Npad values;
-//   1. size-M four-step FFT (column pass reading the short rows, zero beyond), times Bh and
-//      conjugated (row pass), in natural order;
-//   2. size-M four-step FFT, then c[q] conj(G[q]) for q < N stored fftshifted (row pass).
+//   1. the first size-M transform's column pass (reading the short rows, zero beyond), then the
+//      fused middle pass (row DFT, times Bh and conjugated, the second transform's row DFT);
+//   2. the second transform's column pass, c[j] conj(G[j]) for j < N stored fftshifted.
 // Workspace: [x padded | y' padded | W1 (Np M) | W2 (Np M)]; X_g lives in W2 (row stride
-// Npad) until the first row pass overwrites it.
+// Npad) until the middle pass overwrites it.
 #include <algorithm>
 
 #include "bluestein.cuh"
@@ -47,10 +47,10 @@ cudaError_t tc_args(bool tc, int M, TcArgs* a) {
 
 // ---------------------------------------------------------------- FAM
 template <int MM, bool TC>
-__global__ void __launch_bounds__(TileShape<MM>::NT)
-k_fam_pairs_any(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, int P, float2* __restrict__ out,
-                const float2* __restrict__ tw, const float2* __restrict__ chirp, const float2* __restrict__ bh,
-                const unsigned char* __restrict__ bmats, unsigned* err) {
+__device__ __forceinline__ void fam_pairs_any_cta(const float2* __restrict__ X, const float2* __restrict__ Y, int Np,
+                                                  int P, float2* __restrict__ out, const float2* __restrict__ tw,
+                                                  const float2* __restrict__ chirp, const float2* __restrict__ bh,
+                                                  const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<MM>;
   using FS = ResidentSmem<MM, TC>;
@@ -62,16 +62,45 @@ k_fam_pairs_any(const float2* __restrict__ X, const float2* __restrict__ Y, int 
 }
 
 template <int MM, bool TC>
+__global__ void __launch_bounds__(TileShape<MM>::NT)
+k_fam_pairs_any(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, int P, float2* __restrict__ out,
+                const float2* __restrict__ tw, const float2* __restrict__ chirp, const float2* __restrict__ bh,
+                const unsigned char* __restrict__ bmats, unsigned* err) {
+  fam_pairs_any_cta<MM, TC>(X, Y, Np, P, out, tw, chirp, bh, bmats, err);
+}
+
+// The same kernel held to 128 registers per thread, so that two 256-thread CTAs share an SM.
+template <int MM, bool TC>
+__global__ void __launch_bounds__(TileShape<MM>::NT, 2)
+k_fam_pairs_any_2cta(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, int P,
+                     float2* __restrict__ out, const float2* __restrict__ tw, const float2* __restrict__ chirp,
+                     const float2* __restrict__ bh, const unsigned char* __restrict__ bmats, unsigned* err) {
+  fam_pairs_any_cta<MM, TC>(X, Y, Np, P, out, tw, chirp, bh, bmats, err);
+}
+
+template <class K>
+cudaError_t launch_fam_any_k(K kernel, int smem, int NT, int C, const float2* X, const float2* Y, int Np, int P,
+                             float2* out, const float2* tw, const float2* chirp, const float2* bh, TcArgs t,
+                             cudaStream_t st) {
+  cudaError_t e = set_smem(kernel, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t npairs = (int64_t)Np * Np;
+  kernel<<<(unsigned)((npairs + C - 1) / C), NT, smem, st>>>(X, Y, Np, P, out, tw, chirp, bh, t.bm, t.err);
+  return cudaGetLastError();
+}
+
+// The FP32 form from MM = 2048 runs two CTAs per SM (Np = 256, P = 1000: 0.86 -> 0.64 ms;
+// Np = 64, P = 4000: 0.24 -> 0.21 ms); below MM = 2048 the register cap spills, and the
+// tensor-core form lost time under it.
+template <int MM, bool TC>
 cudaError_t launch_fam_any(const float2* X, const float2* Y, int Np, int P, float2* out, const float2* tw,
                            const float2* chirp, const float2* bh, TcArgs t, cudaStream_t st) {
   using S = TileShape<MM>;
   constexpr int sm = ResidentSmem<MM, TC>::total;
-  cudaError_t e = set_smem(k_fam_pairs_any<MM, TC>, sm);
-  if (e != cudaSuccess) return e;
-  const int64_t npairs = (int64_t)Np * Np;
-  k_fam_pairs_any<MM, TC><<<(unsigned)((npairs + S::C - 1) / S::C), S::NT, sm, st>>>(X, Y, Np, P, out, tw, chirp, bh,
-                                                                                   t.bm, t.err);
-  return cudaGetLastError();
+  if constexpr (!TC && MM >= 2048 && S::NT <= 256)
+    return launch_fam_any_k(k_fam_pairs_any_2cta<MM, TC>, sm, S::NT, S::C, X, Y, Np, P, out, tw, chirp, bh, t, st);
+  else
+    return launch_fam_any_k(k_fam_pairs_any<MM, TC>, sm, S::NT, S::C, X, Y, Np, P, out, tw, chirp, bh, t, st);
 }
 
 // ---------------------------------------------------------------- SSCA
@@ -92,95 +121,110 @@ k_bl_prep(const float2* __restrict__ x, const float2* __restrict__ y, int conj, 
   }
 }
 
-template <int M1, bool TC>
+template <int M1, bool TC, bool FINAL>
 __global__ void __launch_bounds__(TileShape<M1>::NT)
-k_bl_cols(const float2* __restrict__ in, int64_t ld, int64_t nvalid, float2* __restrict__ out, int M, int M2,
-          const float2* __restrict__ wM, const float2* __restrict__ cols, const float2* __restrict__ tw,
-          const unsigned char* __restrict__ bmats, unsigned* err) {
+k_bl_cols(const float2* __restrict__ in, int64_t ld, int64_t nvalid, float2* __restrict__ out, int64_t ldo, int64_t M,
+          int M2, int64_t N, const float2* __restrict__ wM, const float2* __restrict__ cols,
+          const float2* __restrict__ chirp, const float2* __restrict__ tw, const unsigned char* __restrict__ bmats,
+          unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<M1>;
   using FS = FftSmem<M1, S::C, S::NT, TC>;
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  bl_cols_tile<M1, TC>(sm, ctx, in + (int64_t)blockIdx.y * ld, nvalid, out + (int64_t)blockIdx.y * M, M, M2, wM, cols,
-                       tw, blockIdx.x * S::C);
+  bl_cols_tile<M1, TC, FINAL>(sm, ctx, in + (int64_t)blockIdx.y * ld, nvalid, out + (int64_t)blockIdx.y * ldo, M, M2, N,
+                              wM, cols, chirp, tw, blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int M2, bool TC, bool FINAL>
-__global__ void __launch_bounds__(TileShape<M2>::NT)
-k_bl_rows(const float2* __restrict__ in, float2* __restrict__ out, int M1, int64_t M, int64_t N,
-          const float2* __restrict__ tw, const float2* __restrict__ lut, const unsigned char* __restrict__ bmats,
-          unsigned* err) {
+template <int M2, bool TC>
+__device__ __forceinline__ void bl_mid_cta(const float2* __restrict__ in, float2* __restrict__ out, int64_t M,
+                                           const float2* __restrict__ tw, const float2* __restrict__ bhr,
+                                           const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<M2>;
-  using FS = FftSmem<M2, S::C, S::NT, TC, rows_stage_bytes<M2>()>;
+  using FS = ResidentSmem<M2, TC>;
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  bl_rows_tile<M2, TC, FINAL>(sm, ctx, in + (int64_t)blockIdx.y * M, out + (int64_t)blockIdx.y * (FINAL ? N : M), M1,
-                              N, tw, lut, blockIdx.x * S::C);
+  bl_mid_tile<M2, TC>(sm, ctx, in + (int64_t)blockIdx.y * M, out + (int64_t)blockIdx.y * M, tw, bhr, blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int MV, bool TC>
-cudaError_t launch_cols_t(const float2* in, int64_t ld, int64_t nvalid, float2* out, int M, int Np, int M1, int M2,
-                          cudaStream_t st) {
+// Tensor-core form: registers as the compiler picks them.
+template <int M2>
+__global__ void __launch_bounds__(TileShape<M2>::NT)
+k_bl_mid_tc(const float2* __restrict__ in, float2* __restrict__ out, int64_t M, const float2* __restrict__ tw,
+            const float2* __restrict__ bhr, const unsigned char* __restrict__ bmats, unsigned* err) {
+  bl_mid_cta<M2, true>(in, out, M, tw, bhr, bmats, err);
+}
+
+// FP32 form: two CTAs per SM (N = 500,000, Np = 256: 3.81 -> 3.52 ms per estimate).
+template <int M2>
+__global__ void __launch_bounds__(TileShape<M2>::NT, 2)
+k_bl_mid_f32(const float2* __restrict__ in, float2* __restrict__ out, int64_t M, const float2* __restrict__ tw,
+             const float2* __restrict__ bhr, const unsigned char* __restrict__ bmats, unsigned* err) {
+  bl_mid_cta<M2, false>(in, out, M, tw, bhr, bmats, err);
+}
+
+// Column pass of either transform over Np channel rows: in rows of stride ld (first nvalid
+// values given), out rows of stride ldo.
+template <int MV, bool TC, bool FINAL>
+cudaError_t launch_cols_t(const float2* in, int64_t ld, int64_t nvalid, float2* out, int64_t ldo, int64_t M, int64_t N,
+                          int Np, int M1, int M2, const float2* chirp, cudaStream_t st) {
   using S = TileShape<MV>;
   cudaError_t err;
   TcArgs t;
   if ((err = tc_args(TC, M1, &t)) != cudaSuccess) return err;
-  const float2* wM = table_roots(M, &err);
+  const float2* wM = table_roots((int)M, &err);
   if (!wM) return err;
-  const float2* cols = table_cols(M, M1, S::C, &err);
+  const float2* cols = table_cols((int)M, M1, S::C, &err);
   if (!cols) return err;
   const float2* tw = table_pass(M1, &err);
   if (!tw) return err;
   constexpr int sm = FftSmem<MV, S::C, S::NT, TC>::total;
-  if ((err = set_smem(k_bl_cols<MV, TC>, sm)) != cudaSuccess) return err;
-  k_bl_cols<MV, TC><<<dim3(M2 / S::C, Np), S::NT, sm, st>>>(in, ld, nvalid, out, M, M2, wM, cols, tw, t.bm, t.err);
+  if ((err = set_smem(k_bl_cols<MV, TC, FINAL>, sm)) != cudaSuccess) return err;
+  k_bl_cols<MV, TC, FINAL><<<dim3(M2 / S::C, Np), S::NT, sm, st>>>(in, ld, nvalid, out, ldo, M, M2, N, wM, cols, chirp,
+                                                                   tw, t.bm, t.err);
   return cudaGetLastError();
 }
 
-template <int MV, bool TC, bool FINAL>
-cudaError_t launch_rows_t(const float2* in, float2* out, int M1, int M2, int64_t N, int Np, const float2* lut,
-                          cudaStream_t st) {
+template <int MV, bool TC>
+cudaError_t launch_mid_t(const float2* in, float2* out, int64_t M, int64_t N, int Np, int M1, int M2,
+                         cudaStream_t st) {
   using S = TileShape<MV>;
   cudaError_t err;
   TcArgs t;
   if ((err = tc_args(TC, M2, &t)) != cudaSuccess) return err;
   const float2* tw = table_pass(M2, &err);
   if (!tw) return err;
-  constexpr int sm = FftSmem<MV, S::C, S::NT, TC, rows_stage_bytes<MV>()>::total;
-  if ((err = set_smem(k_bl_rows<MV, TC, FINAL>, sm)) != cudaSuccess) return err;
-  k_bl_rows<MV, TC, FINAL><<<dim3(M1 / S::C, Np), S::NT, sm, st>>>(in, out, M1, (int64_t)M1 * M2, N, tw, lut, t.bm,
-                                                                   t.err);
+  const float2* bhr = table_bluestein_rows(N, M, M1, &err);
+  if (!bhr) return err;
+  constexpr int sm = ResidentSmem<MV, TC>::total;
+  auto kernel = TC ? k_bl_mid_tc<MV> : k_bl_mid_f32<MV>;
+  if ((err = set_smem(kernel, sm)) != cudaSuccess) return err;
+  kernel<<<dim3(M1 / S::C, Np), S::NT, sm, st>>>(in, out, M, tw, bhr, t.bm, t.err);
   return cudaGetLastError();
 }
 
-template <bool TC>
-cudaError_t launch_cols(const float2* in, int64_t ld, int64_t nvalid, float2* out, int M, int Np, int M1, int M2,
-                        cudaStream_t st) {
+template <bool TC, bool FINAL>
+cudaError_t launch_cols(const float2* in, int64_t ld, int64_t nvalid, float2* out, int64_t ldo, int64_t M, int64_t N,
+                        int Np, int M1, int M2, const float2* chirp, cudaStream_t st) {
   switch (M1) {
-    case 64: return launch_cols_t<64, TC>(in, ld, nvalid, out, M, Np, M1, M2, st);
-    case 128: return launch_cols_t<128, TC>(in, ld, nvalid, out, M, Np, M1, M2, st);
-    case 256: return launch_cols_t<256, TC>(in, ld, nvalid, out, M, Np, M1, M2, st);
-    case 512: return launch_cols_t<512, TC>(in, ld, nvalid, out, M, Np, M1, M2, st);
-    case 1024: return launch_cols_t<1024, TC>(in, ld, nvalid, out, M, Np, M1, M2, st);
+#define SCD_BC(MV) case MV: return launch_cols_t<MV, TC, FINAL>(in, ld, nvalid, out, ldo, M, N, Np, M1, M2, chirp, st);
+    SCD_BC(64) SCD_BC(128) SCD_BC(256) SCD_BC(512) SCD_BC(1024)
+#undef SCD_BC
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <bool TC, bool FINAL>
-cudaError_t launch_rows(const float2* in, float2* out, int M1, int M2, int64_t N, int Np, const float2* lut,
-                        cudaStream_t st) {
+template <bool TC>
+cudaError_t launch_mid(const float2* in, float2* out, int64_t M, int64_t N, int Np, int M1, int M2, cudaStream_t st) {
   switch (M2) {
-    case 64: return launch_rows_t<64, TC, FINAL>(in, out, M1, M2, N, Np, lut, st);
-    case 128: return launch_rows_t<128, TC, FINAL>(in, out, M1, M2, N, Np, lut, st);
-    case 256: return launch_rows_t<256, TC, FINAL>(in, out, M1, M2, N, Np, lut, st);
-    case 512: return launch_rows_t<512, TC, FINAL>(in, out, M1, M2, N, Np, lut, st);
-    case 1024: return launch_rows_t<1024, TC, FINAL>(in, out, M1, M2, N, Np, lut, st);
+#define SCD_BM(MV) case MV: return launch_mid_t<MV, TC>(in, out, M, N, Np, M1, M2, st);
+    SCD_BM(64) SCD_BM(128) SCD_BM(256) SCD_BM(512) SCD_BM(1024)
+#undef SCD_BM
     default: return cudaErrorInvalidValue;
   }
 }
@@ -274,16 +318,14 @@ cudaError_t ssca_any_cdp(const float2* x, const float2* y, bool conj, int64_t N,
 
 cudaError_t ssca_any_first(int64_t N, int Np, void* ws, cudaStream_t st, int precision) {
   const AnyLayout a = any_layout(N, Np, ws);
-  cudaError_t err;
-  const float2* bh = table_bluestein(N, a.M, &err);
-  if (!bh) return err;
   const bool tc = precision == SCD_SPLIT_BF16;
   count_launches(2);
-  err = tc ? launch_cols<true>(a.w2, a.Npad, a.Npad, a.w1, (int)a.M, Np, a.M1, a.M2, st)
-           : launch_cols<false>(a.w2, a.Npad, a.Npad, a.w1, (int)a.M, Np, a.M1, a.M2, st);
+  // first transform's column pass: X_g (rows of Npad values) -> W1; fused middle: W1 -> W2
+  cudaError_t err = tc ? launch_cols<true, false>(a.w2, a.Npad, a.Npad, a.w1, a.M, a.M, N, Np, a.M1, a.M2, nullptr, st)
+                       : launch_cols<false, false>(a.w2, a.Npad, a.Npad, a.w1, a.M, a.M, N, Np, a.M1, a.M2, nullptr, st);
   if (err != cudaSuccess) return err;
-  return tc ? launch_rows<true, false>(a.w1, a.w2, a.M1, a.M2, N, Np, bh, st)
-            : launch_rows<false, false>(a.w1, a.w2, a.M1, a.M2, N, Np, bh, st);
+  return tc ? launch_mid<true>(a.w1, a.w2, a.M, N, Np, a.M1, a.M2, st)
+            : launch_mid<false>(a.w1, a.w2, a.M, N, Np, a.M1, a.M2, st);
 }
 
 cudaError_t ssca_any_second(int64_t N, int Np, void* ws, float2* out, cudaStream_t st, int precision) {
@@ -292,12 +334,10 @@ cudaError_t ssca_any_second(int64_t N, int Np, void* ws, float2* out, cudaStream
   const float2* chirp = table_chirp(N, &err);
   if (!chirp) return err;
   const bool tc = precision == SCD_SPLIT_BF16;
-  count_launches(2);
-  err = tc ? launch_cols<true>(a.w2, a.M, a.M, a.w1, (int)a.M, Np, a.M1, a.M2, st)
-           : launch_cols<false>(a.w2, a.M, a.M, a.w1, (int)a.M, Np, a.M1, a.M2, st);
-  if (err != cudaSuccess) return err;
-  return tc ? launch_rows<true, true>(a.w1, out, a.M1, a.M2, N, Np, chirp, st)
-            : launch_rows<false, true>(a.w1, out, a.M1, a.M2, N, Np, chirp, st);
+  count_launches(1);
+  // second transform's column pass: W2 -> the fftshifted output (rows of N values)
+  return tc ? launch_cols<true, true>(a.w2, a.M, a.M, out, N, a.M, N, Np, a.M1, a.M2, chirp, st)
+            : launch_cols<false, true>(a.w2, a.M, a.M, out, N, a.M, N, Np, a.M1, a.M2, chirp, st);
 }
 
 }  // namespace scd

@@ -13,7 +13,7 @@
 //
 // Two users: the FAM pair transform for any P (both FFTs inside one CTA, the intermediate in the
 // transform's own shared-memory exchange region), and the SSCA strip transform for any N (two
-// four-step FFTs of size M = M1 M2 through global memory, as the power-of-two strip transform).
+// four-step FFTs of size M = M1 M2 through global memory whose row passes are fused).
 #pragma once
 #include "tiles.cuh"
 
@@ -107,61 +107,73 @@ __device__ __forceinline__ void fam_pairs_any_tile(float2* sm, TcCtx& ctx, const
 }
 
 // ---------------------------------------------------------------- SSCA strip transform, any N
-// Column pass of a size-M = M1 M2 four-step transform (n = m1 M2 + m2) over one channel row
-// `in` whose first `nvalid` values are given (row stride >= nvalid; zero beyond): M1-point DFT
-// over m1 for the tile's columns m20 .. m20 + C - 1, times W_M^{(m2 m1') mod M}, to `out` at
-// [m1'][m2] (row of M values).  wM = W_M^j, cols = W_M^{c m1'} at [m1'][c].
-template <int M1, bool TC>
+// The cyclic convolution runs as two size-M four-step transforms (M = M1 M2) sharing their
+// middle: with n = m1 M2 + m2, q = q1 + M1 q2 and j = j2 + M2 j1,
+//   A[q1 + M1 q2] = sum_{m2} W_M2^{q2 m2} W_M^{q1 m2} sum_{m1} W_M1^{q1 m1} a[m1 M2 + m2]
+//   G[j2 + M2 j1] = sum_{q1} W_M1^{j1 q1} W_M^{j2 q1} sum_{q2} W_M2^{j2 q2} B[q1 + M1 q2]
+// so the first transform's row DFT (over m2 -> q2 in row q1), the product B = conj(A Bh) and
+// the second transform's row DFT (over q2 -> j2 in the same row q1) all touch one row: they
+// run as one pass, and the data crosses HBM three times instead of four.
+//
+// Column passes (interleaved columns m2 = m20 + c of one channel row, M1-point DFT over m1):
+//   FINAL = false:  in = the X_g row, first `nvalid` values given (zero beyond);
+//                   out[m1' M2 + m2] = W_M^{m2 m1'} DFT(...)[m1']
+//   FINAL = true:   in = the middle pass's rows, input m1 taken times W_M^{m2 m1};
+//                   G[j] at j = m2 + M2 m1' for j < N: out[(j + N/2) mod N] = c[j] conj(G[j])
+// wM = W_M^j, cols = W_M^{c m1} at [m1][c], chirp = c[j].
+template <int M1, bool TC, bool FINAL>
 __device__ __forceinline__ void bl_cols_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ in, int64_t nvalid,
-                                             float2* __restrict__ out, int M, int M2, const float2* __restrict__ wM,
-                                             const float2* __restrict__ cols, const float2* __restrict__ tw, int m20) {
+                                             float2* __restrict__ out, int64_t M, int M2, int64_t N,
+                                             const float2* __restrict__ wM, const float2* __restrict__ cols,
+                                             const float2* __restrict__ chirp, const float2* __restrict__ tw,
+                                             int m20) {
   using S = TileShape<M1>;
   constexpr int C = S::C;
   const int c = (int)threadIdx.x % C;                            // interleaved columns: c = tid % C
   const int m2 = m20 + c;
-  float2* ob = out + m2;
   const float2* __restrict__ colc = cols + c;
-  auto src = [&](int, int m1) -> float2 {
-    const int64_t n = (int64_t)m1 * M2 + m2;
-    return n < nvalid ? __ldg(in + n) : make_float2(0.f, 0.f);
-  };
-  auto dst = [&](int, int f, float2 v) {
-    const float2 w = cmul(__ldg(wM + ((m20 * f) & (M - 1))), __ldg(colc + f * C));   // W_M^{(m20+c) f}
-    ob[(int64_t)f * M2] = cmul(v, w);
-  };
-  tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  // W_M^{(m20 + c) m1} = W_M^{m20 m1} W_M^{c m1}
+  auto rot = [&](int m1) { return cmul(__ldg(wM + (((int64_t)m20 * m1) & (M - 1))), __ldg(colc + m1 * C)); };
+  if constexpr (!FINAL) {
+    float2* ob = out + m2;
+    auto src = [&](int, int m1) -> float2 {
+      const int64_t n = (int64_t)m1 * M2 + m2;
+      return n < nvalid ? __ldg(in + n) : make_float2(0.f, 0.f);
+    };
+    auto dst = [&](int, int f, float2 v) { ob[(int64_t)f * M2] = cmul(v, rot(f)); };
+    tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  } else {
+    const int64_t half = N / 2;
+    auto src = [&](int, int m1) -> float2 { return cmul(__ldg(in + (int64_t)m1 * M2 + m2), rot(m1)); };
+    auto dst = [&](int, int f, float2 v) {
+      const int64_t j = m2 + (int64_t)M2 * f;
+      if (j < N) out[j + half < N ? j + half : j + half - N] = cmulc(__ldg(chirp + j), v);
+    };
+    tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  }
 }
 
-// Row pass of the same transform: rows r0 .. r0 + C - 1 of `in` ([m1'][m2]), M2-point DFT over
-// m2, bin q = m1' + M1 m2' (natural order), transposed through shared memory so that the C
-// rows' results leave as runs of C consecutive bins.
-//   FINAL = false: out[q] = conj(G[q] Bh[q])                  (q < M, the first transform)
-//   FINAL = true:  out[(q + N/2) mod N] = c[q] conj(G[q])     (q < N, the strip transform's bins)
-template <int M2, bool TC, bool FINAL>
-__device__ __forceinline__ void bl_rows_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ in,
-                                             float2* __restrict__ out, int M1, int64_t N,
-                                             const float2* __restrict__ tw, const float2* __restrict__ lut, int r0) {
+// Middle pass: rows r0 .. r0 + C - 1 of one channel (row q1 of [q1][m2], t-fast): M2-point
+// DFT over m2 -> q2, times bhr[q1][q2] = Bh[q1 + M1 q2] and conjugated in the transform's
+// shared-memory region, M2-point DFT over q2 -> j2, written back as row q1 of `out`.
+template <int M2, bool TC>
+__device__ __forceinline__ void bl_mid_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ in,
+                                            float2* __restrict__ out, const float2* __restrict__ tw,
+                                            const float2* __restrict__ bhr, int r0) {
   using S = TileShape<M2>;
-  constexpr int C = S::C;
-  const float2* __restrict__ rowp = in + (int64_t)(r0 + (int)threadIdx.x / S::T) * M2;   // t-fast
-  auto src = [&](int, int m2) -> float2 { return __ldg(rowp + m2); };
-  auto dst = [&](int c, int f, float2 v) { sm[f * (C + 1) + c] = v; };
-  tile_fft<M2, C, false, true, S::NT, TC>(sm, tw, ctx, src, dst);
+  using PI = PlanInfo<M2>;
+  const int c = (int)threadIdx.x / S::T;
+  const int64_t row = (int64_t)(r0 + c) * M2;
+  const float2* __restrict__ rowp = in + row;
+  const float2* __restrict__ bhp = bhr + row;
+  float2* reg = sm + c * PI::stride(S::C);
+  auto src1 = [&](int, int m2) -> float2 { return __ldg(rowp + m2); };
+  auto dst1 = [&](int, int f, float2 v) { reg[PI::pad(f)] = cconj(cmul(v, __ldg(bhp + f))); };
+  tile_fft<M2, S::C, false, true, S::NT, TC>(sm, tw, ctx, src1, dst1);
   __syncthreads();
-  const int64_t half = N / 2;
-  for (int e = threadIdx.x; e < C * M2; e += blockDim.x) {
-    const int c = e % C, f = e / C;
-    const int64_t q = r0 + c + (int64_t)M1 * f;
-    const float2 g = sm[f * (C + 1) + c];
-    if constexpr (FINAL) {
-      if (q < N) {
-        const int64_t sh = q + half < N ? q + half : q + half - N;
-        out[sh] = cmulc(__ldg(lut + q), g);
-      }
-    } else {
-      out[q] = cconj(cmul(g, __ldg(lut + q)));
-    }
-  }
+  float2* __restrict__ orow = out + row;
+  auto dst2 = [&](int, int f, float2 v) { orow[f] = v; };
+  fft_resident<M2, S::C, S::NT, TC>(sm, tw, ctx, dst2);
 }
 
 }  // namespace scd

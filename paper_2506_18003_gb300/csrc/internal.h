@@ -23,6 +23,8 @@ const float* table_hamming(int Np, cudaError_t* err);      // default window, fl
 // chirp c[j] = W_{2N}^{(j^2) mod 2N} (j < N) and Bh = FFT_M(bt) / M (bluestein.cuh)
 const float2* table_chirp(int64_t N, cudaError_t* err);
 const float2* table_bluestein(int64_t N, int64_t M, cudaError_t* err);
+// Bh in row order of the size-M four-step split M = M1 M2: [q1][q2] = Bh[q1 + M1 q2]
+const float2* table_bluestein_rows(int64_t N, int64_t M, int M1, cudaError_t* err);
 // bf16 hi/lo complex-as-real DFT matrices of the radices of a size-M plan (tensor-core form)
 const unsigned char* table_tc_bmats(int M, int* bytes, cudaError_t* err);
 // one word per device, set by kernels whose bounded device-side waits expired

@@ -147,6 +147,14 @@ __global__ void k_scale_round(const double2* __restrict__ in, float2* __restrict
     out[j] = make_float2((float)(in[j].x * inv), (float)(in[j].y * inv));
 }
 
+// Row-major copy of the kernel spectrum for the fused middle pass of the any-N strip transform:
+// out[q1 M2 + q2] = bh[q1 + M1 q2] (a permutation of float values, exact).
+__global__ void k_permute_rows(const float2* __restrict__ bh, float2* __restrict__ out, int64_t M, int64_t M1) {
+  const int64_t M2 = M / M1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = bh[j / M2 + M1 * (j % M2)];
+}
+
 struct Key {
   int dev, kind;
   int64_t a, b, c;
@@ -241,6 +249,15 @@ const float2* table_bluestein(int64_t N, int64_t M, cudaError_t* err) {
     }
     k_scale_round<<<grid_for(M), 256, 0, st>>>(a, (float2*)p, M);
     cudaFreeAsync(buf, st);
+  });
+}
+
+const float2* table_bluestein_rows(int64_t N, int64_t M, int M1, cudaError_t* err) {
+  const float2* bh = table_bluestein(N, M, err);            // built first: get_or_build holds its lock
+  if (!bh) return nullptr;
+  if (M1 <= 0 || M % M1 != 0) { *err = cudaErrorInvalidValue; return nullptr; }
+  return (const float2*)get_or_build(10, N, M, M1, sizeof(float2) * (size_t)M, err, [&](void* p, cudaStream_t st) {
+    k_permute_rows<<<grid_for(M), 256, 0, st>>>(bh, (float2*)p, M, M1);
   });
 }
 
