@@ -112,9 +112,12 @@ typedef struct {
  *   x       complex64[N], N >= (P-1) L + Np (later samples are ignored)
  *   Np      channels, power of two in [16, 256] (the paper's range 2^4..2^8)
  *   L       hop between blocks, 1 <= L
- *   P       blocks, power of two in [2, 16384]
+ *   P       blocks in [2, 16384]: a power of two, or any P <= 8192 (evaluated by Bluestein's
+ *           identity: the P-point DFT as a cyclic convolution of power-of-two length
+ *           M >= 2P - 1, both size-M transforms inside one CTA per channel pair)
  *   window  float32[Np] or NULL (Hamming)
- *   out     complex64[Np][Np][P], out[kh][lh][qh] = S(k, l, q)
+ *   out     complex64[Np][Np][P], out[kh][lh][qh] = S(k, l, q), qh = q + floor(P/2) with
+ *           q in [-floor(P/2), P - floor(P/2)) (for odd P the zero bin sits at (P-1)/2)
  *   opts    workspace >= scd_fam_workspace_bytes(...) bytes (covers every variant and option)
  * Errors: SCD_ERR_ARG (NULL/misaligned pointers, N too short, L < 1),
  *         SCD_ERR_UNSUPPORTED (Np or P out of range / not a power of two, precision),
@@ -134,10 +137,14 @@ SCD_API size_t scd_fam_workspace_bytes(int64_t N, int32_t Np, int32_t L, int32_t
  * conj(x[n]); conjugate estimate (opts->conjugate): y[n] (or x[n]) unconjugated, with the
  * same alpha and f (x near f_k paired with y near q/N: alpha = f_k + q/N).  The N-point transform is the decomposed
  * (four-step) FFT of Sec. III-B-1 (Eq. Chap4_2DFFT) with N = M1 M2.
- *   x       complex64[N], N a power of two in [2^12, 2^20] (Sec. III-B-2's range)
+ *   x       complex64[N], N in [2^12, 2^20] (Sec. III-B-2's range): a power of two, or any
+ *           N <= 2^19, whose N-point transform runs by Bluestein's identity as two four-step
+ *           transforms of power-of-two length M >= 2N - 1 (staged kernels only: with
+ *           opts->schedule = SCD_SCHEDULE_PERSISTENT such an N gives SCD_ERR_UNSUPPORTED)
  *   Np      power of two in [16, 256]
  *   window  float32[Np] or NULL (Hamming)
- *   out     complex64[Np][N], out[kh][sh] = S(k, q)
+ *   out     complex64[Np][N], out[kh][sh] = S(k, q), sh = q + floor(N/2) with
+ *           q in [-floor(N/2), N - floor(N/2))
  *   opts    workspace >= scd_ssca_workspace_bytes(...) bytes
  * Errors as scd_fam. */
 SCD_API scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, void* out,
@@ -155,7 +162,7 @@ SCD_API size_t scd_ssca_workspace_bytes(int64_t N, int32_t Np, int32_t precision
  * ah = (k + l) Q + q + P L; the cells with alpha < -1 (k = l = -Np/2, q < 0) are not kept.
  *   S    complex64[Np][Np][P] (scd_fam's output)
  *   map  float32[2 Np][2 P L], 16-byte aligned, fully overwritten
- * Needs P L divisible by Np and 2 L <= Np (else SCD_ERR_UNSUPPORTED). */
+ * Needs P a power of two, P L divisible by Np and 2 L <= Np (else SCD_ERR_UNSUPPORTED). */
 SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, float* map, const scd_opts* opts);
 
 /* scd_ssca_map: places |S|^map_power of every SSCA cell on the (f, alpha) grid
@@ -163,7 +170,8 @@ SCD_API scd_status scd_fam_map(const void* S, int32_t Np, int32_t L, int32_t P, 
  *   ah = k N/Np + q + N                          (alpha = (ah - N)/N)
  *   fh = floor((k N/Np - q + N) / (2 N / Np))     (f = fh/Np - 1/2, bin width 1/Np)
  *   S    complex64[Np][N] (scd_ssca's output)
- *   map  float32[Np][2 N], 16-byte aligned, fully overwritten (unreached points are 0) */
+ *   map  float32[Np][2 N], 16-byte aligned, fully overwritten (unreached points are 0)
+ * Needs N a power of two (the grid steps by N/Np per channel; else SCD_ERR_UNSUPPORTED). */
 SCD_API scd_status scd_ssca_map(const void* S, int64_t N, int32_t Np, float* map, const scd_opts* opts);
 
 /* ------------------------------------------------------------------------------ alpha profiles
