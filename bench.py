@@ -566,6 +566,45 @@ def run_reference(args):
     return 0
 
 
+def strip_fft_rates(binding, lib, stream, xs, Ss, work, hbm, reps):
+    """The SSCA's N-point strip FFT at N=2^20, Np=256 on its own: the staged schedule's three
+    kernels timed with the library's stage events (channeliser + CDP, column pass, row pass;
+    median of `reps` calls after 2 warm-ups, both forms).  Each four-step pass reads and writes
+    the Np x N intermediate once (design traffic 2 x 8 Np N bytes per pass, which the ncu
+    capture of these kernels at N=2^18 matches within 1%); the fraction is of the measured
+    copy bandwidth."""
+    import numpy as np
+    N, Np = xs.numel(), Ss.shape[0]
+    ev = (ctypes.c_void_p * 4)()
+    binding.check(lib.scd_events_create(4, ev), "events")
+    res = {"N": N, "Np": Np, "schedule": "stages", "bytes_per_pass": 2 * 8 * Np * N}
+    for prec in ("fp32", "split"):
+        o = binding.make_opts(stream, prec, work, schedule="stages")
+        o.stage_events = ctypes.cast(ev, ctypes.POINTER(ctypes.c_void_p))
+        o.n_stage_events = 4
+        xp, op = ctypes.c_void_p(xs.data_ptr()), ctypes.c_void_p(Ss.data_ptr())
+        rows = []
+        for r in range(reps + 2):
+            binding.check(lib.scd_ssca(xp, N, Np, None, op, ctypes.byref(o)), "scd_ssca")
+            if r < 2:
+                continue
+            t = []
+            for i in range(3):
+                f = ctypes.c_float()
+                binding.check(lib.scd_event_elapsed_ms(ev[i], ev[i + 1], ctypes.byref(f)), "elapsed")
+                t.append(f.value)
+            rows.append(t)
+        cdp, cols, rows_ms = (float(v) for v in np.median(np.array(rows), axis=0))
+        per_pass = 2 * 8 * Np * N
+        res[prec] = {"channeliser_cdp_ms": round(cdp, 5), "column_pass_ms": round(cols, 5),
+                     "row_pass_ms": round(rows_ms, 5),
+                     "column_pass_hbm_frac": round(per_pass / (cols * 1e-3) / 1e9 / hbm, 4),
+                     "row_pass_hbm_frac": round(per_pass / (rows_ms * 1e-3) / 1e9 / hbm, 4),
+                     "strip_fft_hbm_frac": round(2 * per_pass / ((cols + rows_ms) * 1e-3) / 1e9 / hbm, 4)}
+    lib.scd_events_destroy(4, ev)
+    return res
+
+
 def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
     """Times the cross / conjugate estimates and the alpha profiles at the paper-scale sizes
     (FAM N=65,728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256), outside the step's timed region:
@@ -617,7 +656,7 @@ def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
                                                       workspace=work),
                              8 * Na + 8 * Nps * Na),
     }
-    out = {}
+    out = {"ssca_strip_fft": strip_fft_rates(binding, lib, stream, xs, Ss, work, hbm, reps)}
     with torch.cuda.stream(stream):
         for name, (fn, nbytes) in cases.items():
             for _ in range(warmup):
