@@ -36,9 +36,9 @@ k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __rest
 }
 
 template <int PP, bool TC>
-__global__ void __launch_bounds__(TileShape<PP>::NT)
-k_fam_pairs(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, float2* __restrict__ out,
-            const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
+__device__ __forceinline__ void fam_pairs_cta(const float2* __restrict__ X, const float2* __restrict__ Y, int Np,
+                                              float2* __restrict__ out, const float2* __restrict__ tw,
+                                              const unsigned char* __restrict__ bmats, unsigned* err) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<PP>;
   using FS = FftSmem<PP, S::C, S::NT, TC>;
@@ -47,6 +47,21 @@ k_fam_pairs(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, 
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
   fam_pairs_tile<PP, TC>(sm, ctx, X, Y, Np, out, tw, (int64_t)blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
+}
+
+template <int PP, bool TC>
+__global__ void __launch_bounds__(TileShape<PP>::NT)
+k_fam_pairs(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, float2* __restrict__ out,
+            const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
+  fam_pairs_cta<PP, TC>(X, Y, Np, out, tw, bmats, err);
+}
+
+// The same kernel with its registers capped so that MINB CTAs share an SM.
+template <int PP, bool TC, int MINB>
+__global__ void __launch_bounds__(TileShape<PP>::NT, MINB)
+k_fam_pairs_capped(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, float2* __restrict__ out,
+                   const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
+  fam_pairs_cta<PP, TC>(X, Y, Np, out, tw, bmats, err);
 }
 
 template <class K>
@@ -66,15 +81,34 @@ cudaError_t launch_k1(const float2* x, int L, int P, const float* window, const 
   return cudaGetLastError();
 }
 
+// CTAs per SM that the FP32 pair kernel's registers are capped for (0: as the compiler picks).
+// Measured at Np = 256 (pair stage, GB300): P = 512 0.074 -> 0.068 ms (3 CTAs, 80 registers),
+// 1024 0.144 -> 0.140 (3), 2048 0.341 -> 0.328 (4, 64 registers), 4096 0.732 -> 0.703 (4),
+// 8192 1.95 -> 1.57 (2, 128 registers: the compiler's 155 left one CTA per SM).
+template <int PV, bool TC>
+struct FamPairsBlocks { static constexpr int value = 0; };
+template <> struct FamPairsBlocks<512, false> { static constexpr int value = 3; };
+template <> struct FamPairsBlocks<1024, false> { static constexpr int value = 3; };
+template <> struct FamPairsBlocks<2048, false> { static constexpr int value = 4; };
+template <> struct FamPairsBlocks<4096, false> { static constexpr int value = 4; };
+template <> struct FamPairsBlocks<8192, false> { static constexpr int value = 2; };
+
+template <int PV, bool TC>
+auto fam_pairs_kernel() {
+  if constexpr (FamPairsBlocks<PV, TC>::value > 0) return k_fam_pairs_capped<PV, TC, FamPairsBlocks<PV, TC>::value>;
+  else return k_fam_pairs<PV, TC>;
+}
+
 template <int PV, bool TC>
 cudaError_t launch_k2(const float2* X, const float2* Y, int Np, float2* out, const float2* tw, const unsigned char* bm,
                       unsigned* err, cudaStream_t st) {
   using S = TileShape<PV>;
   constexpr int sm = FftSmem<PV, S::C, S::NT, TC>::total;
-  cudaError_t e = set_smem(k_fam_pairs<PV, TC>, sm);
+  auto kernel = fam_pairs_kernel<PV, TC>();
+  cudaError_t e = set_smem(kernel, sm);
   if (e != cudaSuccess) return e;
   const int64_t npairs = (int64_t)Np * Np;
-  k_fam_pairs<PV, TC><<<(unsigned)((npairs + S::C - 1) / S::C), S::NT, sm, st>>>(X, Y, Np, out, tw, bm, err);
+  kernel<<<(unsigned)((npairs + S::C - 1) / S::C), S::NT, sm, st>>>(X, Y, Np, out, tw, bm, err);
   return cudaGetLastError();
 }
 
