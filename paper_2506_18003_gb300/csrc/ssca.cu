@@ -197,6 +197,11 @@ void ssca_split(int64_t N, int* M1, int* M2) {
   const int e = ilog2(N);
   *M1 = 1 << ((e + 1) / 2);
   *M2 = 1 << (e / 2);
+  // N = 2^19: 512 x 1024 rather than 1024 x 512.  The 512-point column pass runs at the row
+  // pass's rate, the 1024-point one a third slower per point (staged, Np = 256: 1.181 ->
+  // 1.035 ms per estimate); at 2^20 the split stays 1024 x 1024 (a 2048-point row pass would
+  // write runs of two values and lose more than the column pass gains).
+  if (e == 19) { *M1 = 512; *M2 = 1024; }
 }
 
 cudaError_t ssca_cdp(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window, float2* ws,

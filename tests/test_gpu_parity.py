@@ -201,3 +201,23 @@ def test_ssca_maximum_length_small_np(torch, Np):
     assert float(np.max(np.abs(got - ref))) / smax <= FP32_TOL
     del got_t
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("schedule", ["stages", "persistent"])
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_ssca_2p19_both_schedules(torch, schedule, precision):
+    """N = 2^19 (strip transform split 512 x 1024, the one size where the column pass is the
+    shorter one): 4 full channel rows of both schedules and both forms against the oracle."""
+    N, Np = 1 << 19, 64
+    x = signals.modulated("qpsk", N, 4, 0.1, 5.0, seed=9300)
+    a = orc.hamming_window(Np)
+    got_t = binding.scd_ssca(_dev(torch, x), Np, window=_dev(torch, a), schedule=schedule, precision=precision)
+    binding.scd_check_device()
+    ch = np.array([0, 17, Np // 2, Np - 1])
+    ref = orc.ssca(x, a, Np, channels=ch, chunk=1 << 16)
+    got = got_t[torch.from_numpy(ch).cuda()].cpu().numpy()
+    smax = got_t.abs().max().item()
+    tol = FP32_TOL if precision == "fp32" else 1e-3
+    assert float(np.max(np.abs(got - ref))) / smax <= tol
+    del got_t
+    torch.cuda.empty_cache()
