@@ -317,7 +317,7 @@ scd_status scd_prepare(int32_t estimator, int64_t N, int32_t Np, int32_t P) {
     int M1, M2;
     scd::ssca_split(M, &M1, &M2);
     if (!scd::table_roots((int)M, &e) || !scd::table_pass(M1, &e) || !scd::table_pass(M2, &e) ||
-        !scd::table_cols((int)M, M1, scd::ssca_cols_per_tile(M1), &e))
+        !scd::table_cols((int)M, M1, scd::ssca_cols_per_tile(M1), &e) || !scd::device_error_word(&e))
       return cuda_fail(e);
     if (!scd::is_pow2(N) && (!scd::table_chirp(N, &e) || !scd::table_bluestein_rows(N, M, M1, &e)))
       return cuda_fail(e);

@@ -58,6 +58,10 @@ cudaError_t ssca_cdp(const float2* x, const float2* y, bool conj, int64_t N, int
                      cudaStream_t st, int precision);
 // Stage 1: M1-point column FFTs times the rotate factor, in place on ws
 cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st, int precision);
+// The FP32 column pass with its input staged through TMA (cols_tma.cu), for the M1 where it
+// is the faster one; ws 16-byte aligned, rows of N = M1 M2 values.
+bool ssca_cols_tma_supported(int M1);
+cudaError_t ssca_cols_tma(float2* ws, int64_t N, int Np, int M1, int M2, cudaStream_t st);
 // Stage 2: M2-point row FFTs, fftshifted into out[kh][sh]
 cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st, int precision);
 

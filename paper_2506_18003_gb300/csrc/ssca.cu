@@ -214,6 +214,7 @@ cudaError_t ssca_cols(float2* ws, int64_t N, int Np, cudaStream_t st, int precis
   int M1, M2;
   ssca_split(N, &M1, &M2);
   count_launches(1);
+  if (precision != SCD_SPLIT_BF16 && ssca_cols_tma_supported(M1)) return ssca_cols_tma(ws, N, Np, M1, M2, st);
   return launch_cols(ws, (int)N, Np, M1, M2, precision == SCD_SPLIT_BF16, st);
 }
 

@@ -148,15 +148,19 @@ __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const floa
 // at [m1'][m2].  wN = W_N^j table, cols = W_N^{c m1'} at [m1'][c].
 // DISCARD: the input (X_g) is dead once this tile has read it and `out` is another buffer:
 // the tile's whole L2 lines of it are discarded so that they are never written back.
-// FP32 form: the tile's factors W_N^{m20 f} (f < M1, common to its C columns) are gathered
-// from the W_N table into shared memory (`stage`, M1 values, disjoint from the FFT's buffers)
-// before the transform, whose barriers order them before the last pass reads them.  The split
-// form reads them from the table directly: its larger layout would otherwise outgrow the
-// shared-memory carveout that leaves two CTAs per SM a useful L1.
+// FP32 form: the last pass hands thread (c, t) the bins f = i + p j (p = r0, the first radix;
+// i in [0, p) one of the thread's B = r0/r1 residues, j < r1), so the rotate factor splits as
+//     W_N^{(m20 + c) f} = W_N^{(m20 + c) i} * W_N^{(m20 + c) p j}:
+// the first factor is gathered from the W_N table per thread (B values), the second is shared
+// by the tile's C columns and r1 values of j (C r1 = 256, one per thread), gathered into shared
+// memory (`stage`, [j][c], disjoint from the FFT's buffers) before the transform, whose
+// barriers order it before the last pass reads it.  No per-bin table read remains.  The split
+// form reads W_N^{m20 f} and W_N^{c f} from the tables directly: its larger layout would
+// otherwise outgrow the shared-memory carveout that leaves two CTAs per SM a useful L1.
 template <int M1, bool TC>
 struct ColsStage {
   static constexpr int off = FftSmem<M1, TileShape<M1>::C, TileShape<M1>::NT, TC>::region0;
-  static constexpr int end = off + (TC ? 0 : M1 * 8);
+  static constexpr int end = off + (TC ? 0 : TileShape<M1>::C * PlanInfo<M1>::r1 * 8);
 };
 template <int M1, bool TC>
 using ColsSmem = FftSmem<M1, TileShape<M1>::C, TileShape<M1>::NT, TC, ColsStage<M1, TC>::end>;
@@ -166,21 +170,38 @@ __device__ __forceinline__ void ssca_cols_tile(float2* sm, TcCtx& ctx, const flo
                                                const float2* __restrict__ wN, const float2* __restrict__ cols,
                                                const float2* __restrict__ tw, int m20, float2* stage) {
   using S = TileShape<M1>;
+  using PI = PlanInfo<M1>;
   constexpr int C = S::C;
-  static_assert(PlanInfo<M1>::n >= 2, "the staged factors rely on the transform's barriers");
-  if constexpr (!TC)
-    for (int f = threadIdx.x; f < M1; f += blockDim.x) stage[f] = __ldg(wN + ((m20 * f) & (N - 1)));
+  static_assert(PI::n == 2, "the staged factors rely on the transform's barrier; f = i + r0 j");
   const int c = (int)threadIdx.x % C;                             // interleaved columns: c = tid % C
   const float2* ib = in + m20 + c;
   float2* ob = out + m20 + c;
-  const float2* __restrict__ colc = cols + c;
   auto src = [&](int, int m1) -> float2 { return ib[(int64_t)m1 * M2]; };
-  auto dst = [&](int, int f, float2 v) {
-    const float2 wm = TC ? __ldg(wN + ((m20 * f) & (N - 1))) : stage[f];
-    const float2 w = cmul(wm, __ldg(colc + f * C));               // W_N^{(m20+c) f}
-    ob[(int64_t)f * M2] = cmul(v, w);
-  };
-  tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  if constexpr (TC) {
+    const float2* __restrict__ colc = cols + c;
+    auto dst = [&](int, int f, float2 v) {
+      const float2 w = cmul(__ldg(wN + ((m20 * f) & (N - 1))), __ldg(colc + f * C));   // W_N^{(m20+c) f}
+      ob[(int64_t)f * M2] = cmul(v, w);
+    };
+    tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  } else {
+    constexpr int p = PI::r0, T = PI::T;
+    static_assert(C * PI::r1 == S::NT && (p == T || p == 2 * T), "one staged factor per thread, B <= 2");
+    const int64_t col = m20 + c;
+    {                                                             // stage[j C + cc] = W_N^{(m20 + cc) p j}
+      const int jj = (int)threadIdx.x / C, cc = (int)threadIdx.x % C;
+      stage[threadIdx.x] = __ldg(wN + (((int64_t)(m20 + cc) * p * jj) & (N - 1)));
+    }
+    const int t = (int)threadIdx.x / C;
+    const float2 a0 = __ldg(wN + ((col * t) & (N - 1)));          // W_N^{(m20 + c) i}, i = t, t + T
+    const float2 a1 = p == 2 * T ? __ldg(wN + ((col * (t + T)) & (N - 1))) : a0;
+    auto dst = [&](int, int f, float2 v) {
+      const int i = f & (p - 1), j = f / p;
+      const float2 w = cmul(i < T ? a0 : a1, stage[j * C + c]);   // W_N^{(m20+c) f}
+      ob[(int64_t)f * M2] = cmul(v, w);
+    };
+    tile_fft<M1, C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  }
   if constexpr (DISCARD && C * 8 % 128 == 0) {                   // the tile owns whole lines of each row
     __syncthreads();                                            // every read of the input is done
     constexpr int LPR = C * 8 / 128;                            // lines per row
