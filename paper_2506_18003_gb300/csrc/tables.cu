@@ -22,6 +22,13 @@
 namespace scd {
 namespace {
 
+// Entries of the concatenated pass-twiddle table of a plan with radices (r0, r1, r2) (layout
+// in PlanInfo, fft.cuh; r1 = 0: single pass, no table): the one length that the allocation and
+// the kernel that fills it both use.
+__host__ __device__ constexpr int pass_table_len(int r0, int r1, int r2) {
+  return r1 == 0 ? 0 : r0 * r1 + (r2 ? r0 * r1 * r2 : 0);
+}
+
 __device__ __forceinline__ float2 root_fp64(int64_t j, int64_t M) {
   double s, c;
   sincospi(2.0 * (double)j / (double)M, &s, &c);
@@ -36,7 +43,7 @@ __global__ void k_roots(float2* out, int64_t M) {
 // Stockham pass twiddles: for pass s (s >= 1) with p = prod of earlier radices and radix R,
 // entry off_s + r p + k = W_{pR}^{k r} = W_M^{k r M/(pR)} (k < p, r < R, so the index is < M).
 __global__ void k_pass(float2* out, int M, int r0, int r1, int r2) {
-  const int total = r0 * r1 + (r2 ? r0 * r1 * r2 : 0);
+  const int total = pass_table_len(r0, r1, r2);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x)
     out[e] = root_fp64(pass_twiddle_exponent(e, M, r0, r1, r2), M);
 }
@@ -216,7 +223,7 @@ const float2* table_roots(int M, cudaError_t* err) {
 const float2* table_pass(int M, cudaError_t* err) {
   PassRadices r = pass_radices(M);
   if (r.r0 == 0) { *err = cudaErrorInvalidValue; return nullptr; }
-  int len = r.r1 ? r.r0 * r.r1 + (r.r2 ? r.r0 * r.r1 * r.r2 : 0) : 1;
+  int len = r.r1 ? pass_table_len(r.r0, r.r1, r.r2) : 1;
   return (const float2*)get_or_build(1, M, 0, 0, sizeof(float2) * (size_t)len, err, [&](void* p, cudaStream_t st) {
     if (r.r1) k_pass<<<grid_for(len), 256, 0, st>>>((float2*)p, M, r.r0, r.r1, r.r2);
     else cudaMemsetAsync(p, 0, sizeof(float2), st);
@@ -271,7 +278,7 @@ cudaError_t build_pass_into(float2* out, int M, cudaStream_t st) {
   PassRadices r = pass_radices(M);
   if (r.r0 == 0) return cudaErrorInvalidValue;
   if (!r.r1) return cudaSuccess;                               // single-pass plans use no table
-  const int len = r.r0 * r.r1 + (r.r2 ? r.r0 * r.r1 * r.r2 : 0);
+  const int len = pass_table_len(r.r0, r.r1, r.r2);
   k_pass<<<grid_for(len), 256, 0, st>>>(out, M, r.r0, r.r1, r.r2);
   return cudaGetLastError();
 }
