@@ -60,6 +60,7 @@ SIGNATURES = {
     "scd_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "scd_batch_plan_destroy": (None, [_vp]),
     "scd_batch_plan_set_output": (_i32, [_vp, _i32]),
+    "scd_batch_plan_set_schedule": (_i32, [_vp, _i32]),
     "scd_batch_tune": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "scd_stream_plan_create": (_i32, [_i32, _i64, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_stream_advance": (_i32, [_vp, _vp, _vp, _i32, _vp]),
@@ -337,6 +338,11 @@ class BatchPlan:
         check(self.lib.scd_batch_plan_set_output(self.handle, p), "scd_batch_plan_set_output")
         self.profile_power = p
         self._query()
+
+    def set_schedule(self, schedule: str = "auto"):
+        """SSCA plans: "persistent" (one launch), "stages" (one launch per stage and size) or
+        "auto" (the autotuned choice)."""
+        check(self.lib.scd_batch_plan_set_schedule(self.handle, SCHEDULES[schedule]), "scd_batch_plan_set_schedule")
 
     def out_dtype(self):
         return _torch().float32 if self.profile_power else _torch().complex64

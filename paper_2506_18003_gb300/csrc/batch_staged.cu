@@ -1,0 +1,158 @@
+// Staged schedule of an SSCA batch plan: instead of one persistent launch with a device work
+// queue, one launch per stage and transform size over every signal of the plan, in stream
+// order (no device-side waits): the channeliser + CDP of all signals, then per size class the
+// column passes (in place on each signal's X_g) and the row passes (to the output arena).
+// Each kernel has only its own tile's registers and shared memory, so it runs at the
+// occupancy of the standalone kernels (the column pass's registers capped for 2 CTAs per SM
+// at M1 >= 512, 3 at 128 and 256, 4 below); the price is the X_g round trip through HBM that the
+// persistent schedule's rotating slots avoid.  The autotuner picks the faster of the two.
+//
+// Every kernel runs one CTA tile per CTA (grid = the launch's tiles); task i covers the tiles
+// [first_i, first_i + subtiles_i) and a CTA finds its task by binary search.  (A persistent
+// walk over the tiles kept more state live and spilled in the column pass.)
+#include "batch_kernel.cuh"
+
+namespace scd {
+namespace bk {
+namespace {
+
+// The task of CTA tile `tile`: the last task whose first tile is <= tile (binary search).
+__device__ __forceinline__ int find_task(const Task* __restrict__ tl, int nt, int64_t tile) {
+  int lo = 0, hi = nt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&tl[mid].first) <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int NP, bool TC>
+__global__ void __launch_bounds__(kThreads) k_st_cdp(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  using FS = CdpSmem<NP, TC>;
+  static_assert(TileShape<NP>::NT == kThreads, "one tile per CTA");
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, A.bmats_np, FS::bbytes, A.err);
+  {
+    const int64_t tile = blockIdx.x;
+    const Task& t = tl[find_task(tl, nt, tile)];
+    const int64_t local = tile - t.first;
+    ssca_cdp_tile<NP, TC>(sm, ctx, A.x + t.x_off, A.y + t.x_off, A.conj != 0, t.N, A.window, A.tw_np, A.ws + t.ws_off,
+                          (int)local * TileShape<NP>::C, base + CdpStage<NP, TC>::off);
+  }
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
+}
+
+// Column passes of one size class (all tasks share N, M1, M2 and the tables).
+template <int M1, bool TC>
+__global__ void __launch_bounds__(kThreads, M1 >= 512 ? 2 : (M1 >= 128 ? 3 : 4)) k_st_cols(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  using S = TileShape<M1>;
+  using FS = ColsSmem<M1, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, tl[0].bmats, FS::bbytes, A.err);
+  {
+    const int64_t tile = blockIdx.x;
+    const Task& t = tl[find_task(tl, nt, tile)];
+    const int64_t local = tile - t.first;
+    const int per = t.M2 / S::C;
+    const int64_t kh = local / per;
+    float2* row = A.ws + t.ws_off + kh * t.N;
+    ssca_cols_tile<M1, TC>(sm, ctx, row, row, t.N, t.M2, t.wN, t.cols, t.tw, (int)(local % per) * S::C,
+                           reinterpret_cast<float2*>(base + ColsStage<M1, TC>::off));
+  }
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
+}
+
+// Row passes of one size class.
+template <int M2, bool TC>
+__global__ void __launch_bounds__(kThreads) k_st_rows(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  using S = TileShape<M2>;
+  using FS = FftSmem<M2, S::C, S::NT, TC, rows_stage_bytes<M2>()>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, tl[0].bmats, FS::bbytes, A.err);
+  {
+    const int64_t tile = blockIdx.x;
+    const Task& t = tl[find_task(tl, nt, tile)];
+    const int64_t local = tile - t.first;
+    const int per = t.M1 / S::C;
+    const int64_t kh = local / per;
+    ssca_rows_tile<M2, TC>(sm, ctx, A.ws + t.ws_off + kh * t.N, A.out + t.out_off + kh * t.N, t.M1, t.tw,
+                           (int)(local % per) * S::C);
+  }
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
+}
+
+template <class K>
+cudaError_t prepare_t(K kernel, int smem, bool tc, int* smem_out, int* per_sm) {
+  *smem_out = smem;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, kThreads, smem);
+  // the query answers one for kernels that allocate tensor memory; two CTAs of at most 128
+  // TMEM columns always fit (as for the persistent kernel)
+  if (tc && *per_sm < 2) *per_sm = 2;
+  return e;
+}
+
+template <int M, bool TC>
+cudaError_t prep_m(int kind, int* smem, int* per_sm) {
+  if constexpr (M <= 256)
+    if (kind == 0) return prepare_t(k_st_cdp<M, TC>, CdpSmem<M, TC>::total, TC, smem, per_sm);
+  if constexpr (M >= 64) {
+    using S = TileShape<M>;
+    if (kind == 1) return prepare_t(k_st_cols<M, TC>, ColsSmem<M, TC>::total, TC, smem, per_sm);
+    if (kind == 2)
+      return prepare_t(k_st_rows<M, TC>, FftSmem<M, S::C, S::NT, TC, rows_stage_bytes<M>()>::total, TC, smem, per_sm);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int M, bool TC>
+void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, int nt, int64_t total, cudaStream_t st) {
+  if constexpr (M <= 256)
+    if (kind == 0) k_st_cdp<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  if constexpr (M >= 64) {
+    if (kind == 1) k_st_cols<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    if (kind == 2) k_st_rows<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  }
+}
+
+// kinds: 0 channeliser (M = Np in 16..256), 1 column pass (M = M1), 2 row pass (M = M2), M1 and
+// M2 in 64..1024
+bool valid(int kind, int M) {
+  if (kind == 0) return M == 16 || M == 32 || M == 64 || M == 128 || M == 256;
+  return M == 64 || M == 128 || M == 256 || M == 512 || M == 1024;
+}
+
+}  // namespace
+
+cudaError_t staged_prepare(int kind, int M, bool tc, int* smem, int* per_sm) {
+  if (!valid(kind, M)) return cudaErrorInvalidValue;
+#define SCD_SP(MV) case MV: return tc ? prep_m<MV, true>(kind, smem, per_sm) : prep_m<MV, false>(kind, smem, per_sm);
+  switch (M) {
+    SCD_SP(16) SCD_SP(32) SCD_SP(64) SCD_SP(128) SCD_SP(256) SCD_SP(512) SCD_SP(1024)
+    default: return cudaErrorInvalidValue;
+  }
+#undef SCD_SP
+}
+
+cudaError_t staged_launch(int kind, int M, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl, int nt,
+                          int64_t total, cudaStream_t st) {
+  if (!valid(kind, M)) return cudaErrorInvalidValue;
+#define SCD_SL(MV) case MV: if (tc) launch_m<MV, true>(kind, grid, smem, A, tl, nt, total, st); else launch_m<MV, false>(kind, grid, smem, A, tl, nt, total, st); break;
+  switch (M) {
+    SCD_SL(16) SCD_SL(32) SCD_SL(64) SCD_SL(128) SCD_SL(256) SCD_SL(512) SCD_SL(1024)
+    default: return cudaErrorInvalidValue;
+  }
+#undef SCD_SL
+  return cudaGetLastError();
+}
+
+}  // namespace bk
+}  // namespace scd

@@ -98,7 +98,8 @@ cudaError_t ssca_alpha_profile(const float2* S, int64_t N, int Np, int power, fl
 
 // ---------------------------------------------------------------- autotuner cache (tune.cu)
 struct TuneEntry {
-  int schedule;           // scd_schedule for single SSCA calls; 0 for batch plans
+  int schedule;           // scd_schedule for single SSCA calls; batch plans: 1 = the SSCA
+                          // staged schedule (batch_staged.cu), else 0
   int64_t item_bytes;     // output bytes per persistent-queue item
   int64_t slot_bytes;     // bytes of one SSCA column-pass slot
   double ms;              // measured time of the choice

@@ -3,6 +3,7 @@
     python -m paper_2506_18003_gb300.profile_case ssca --N 262144 --Np 256 --reps 3
     python -m paper_2506_18003_gb300.profile_case fam --N 65728 --Np 256 --L 64 --P 1024 --reps 3
     python -m paper_2506_18003_gb300.profile_case batch_fam --N 0 --Np 64 --L 16 --nsig 64 --reps 2
+    python -m paper_2506_18003_gb300.profile_case batch_ssca --N 0 --Np 128 --nsig 32 --schedule stages
 
 Inputs are seeded white noise (the kernels' cost does not depend on the values).  Prints
 the CUDA-event time of each call.
@@ -30,12 +31,15 @@ def main() -> int:
     ap.add_argument("--P", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--schedule", default="auto", help="batch_ssca: auto, stages or persistent")
     a = ap.parse_args()
 
     if a.estimator.startswith("batch_"):
         est = a.estimator[6:]
         lengths = [int(v) for v in signals.batch_lengths(a.nsig)]
         plan = binding.BatchPlan(est, lengths, a.Np, a.L, a.precision)
+        if est == "ssca":
+            plan.set_schedule(a.schedule)
         xa = torch.from_numpy(signals.awgn(int(sum(lengths)), seed=99)).cuda()
         out = torch.empty(plan.out_offsets[-1], dtype=torch.complex64, device="cuda")
         ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")

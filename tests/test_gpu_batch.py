@@ -118,3 +118,28 @@ def test_batch_512_signals_subset(torch):
         err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
         assert err <= TOL["fp32"], (i, err)
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_ssca_batch_staged_schedule(torch, precision):
+    """The staged schedule (one launch per stage and size class) against the FP64 oracle for
+    every signal, and bit for bit against the persistent schedule (same tile arithmetic)."""
+    Np = 64
+    lengths = [4096, 70000, 9000, 4200, 150000, 33000, 8192]
+    sigs = [signals.batch_signal(300 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("ssca", lengths, Np, 1, precision)
+    plan.set_schedule("persistent")
+    _, out_p, _ = _run(torch, plan, sigs)
+    plan.set_schedule("stages")
+    _, out_s, _ = _run(torch, plan, sigs)
+    assert torch.equal(out_p, out_s)
+    a = orc.hamming_window(Np)
+    for i, x in enumerate(sigs):
+        N = plan.sizes[i]
+        ref = orc.ssca(x[:N].copy(), a, Np)
+        got = plan.output(out_s, i).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL[precision], (i, err)
+    with pytest.raises(binding.ScdError):
+        binding.BatchPlan("fam", [4096], 64, 16).set_schedule("stages")
+    plan.close()

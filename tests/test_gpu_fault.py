@@ -25,6 +25,8 @@ def test_dropped_task_times_out_and_recovers(torch, monkeypatch, estimator, Np, 
     lengths = [4096, 5000]
     sigs = [signals.batch_signal(500 + i, n) for i, n in enumerate(lengths)]
     plan = binding.BatchPlan(estimator, lengths, Np, L)
+    if estimator == "ssca":
+        plan.set_schedule("persistent")                      # the schedule with device-side waits
     x = torch.from_numpy(np.concatenate(sigs)).cuda()
     out = torch.empty(plan.out_offsets[-1], dtype=torch.complex64, device="cuda")
     ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
