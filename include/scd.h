@@ -189,10 +189,10 @@ SCD_API scd_status scd_ssca_alpha_profile(const void* S, int64_t N, int32_t Np, 
 
 /* ------------------------------------------------------------------------------ batches
  * Batched form: nsig signals of uneven lengths through ONE persistent kernel launch (a
- * device work queue of per-signal stage tiles with bounded dependency waits), or for SSCA full
- * estimates by default the staged schedule (one launch per stage and transform size over all
- * signals, see scd_batch_plan_set_schedule), captured in a CUDA graph that later runs with
- * the same buffers and stream replay.
+ * device work queue of per-signal stage tiles with bounded dependency waits), or the staged
+ * schedule (one launch per stage and transform size over all signals; the default for SSCA
+ * full estimates, see scd_batch_plan_set_schedule), captured in a CUDA graph that later runs
+ * with the same buffers and stream replay.
  *   estimator  0 = FAM (Np, L), 1 = SSCA (Np; L ignored)
  *   lengths    HOST array of nsig signal lengths (samples)
  *   Np         power of two in [16, 256]; precision: scd_precision
@@ -231,12 +231,13 @@ SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
  * out arena is float32[out_offsets[nsig]], zeroed by every run.  FAM needs 2 L <= Np and
  * P_i L divisible by Np for every signal (else SCD_ERR_UNSUPPORTED). */
 SCD_API scd_status scd_batch_plan_set_output(scd_batch_plan* plan, int32_t mode);
-/* Schedule of an SSCA plan's full estimates (scd_schedule): SCD_SCHEDULE_PERSISTENT = the one
- * persistent launch (column-pass output in rotating L2-sized slots); SCD_SCHEDULE_STAGES = one
- * launch per stage and transform size over all signals (the channelisers, then per N_i the
- * column passes in place on the workspace and the row passes; same workspace, no device-side
- * waits); SCD_SCHEDULE_AUTO = the autotuner's choice for this workload, else STAGES (the
- * default of new SSCA plans).  FAM plans, and alpha-profile output, always run persistent
+/* Schedule of a plan's full estimates (scd_schedule): SCD_SCHEDULE_PERSISTENT = the one
+ * persistent launch (SSCA: column-pass output in rotating L2-sized slots);
+ * SCD_SCHEDULE_STAGES = one launch per stage and transform size over all signals (the
+ * channelisers, then per size class the SSCA column passes in place on the workspace and row
+ * passes, or the FAM pair transforms; same workspace, no device-side waits);
+ * SCD_SCHEDULE_AUTO = the autotuner's choice for this workload, else the default of new plans
+ * (STAGES for SSCA, PERSISTENT for FAM).  Alpha-profile output always runs persistent
  * (STAGES: SCD_ERR_UNSUPPORTED). */
 SCD_API scd_status scd_batch_plan_set_schedule(scd_batch_plan* plan, int32_t schedule);
 
@@ -272,9 +273,9 @@ SCD_API scd_status scd_stream_advance(scd_batch_plan* plan, void* x_arena, const
  * from which later processes start.  Both calls enqueue and time real runs on `stream`
  * (the outputs hold a valid estimate afterwards) and synchronise it.
  *
- * scd_batch_tune: items of 32..512 KiB, SSCA slots of 8..64 MiB, and for SSCA full estimates
- *   the staged schedule; re-plans `plan` with the fastest setting (plans created later for
- *   the same workload start from it).
+ * scd_batch_tune: items of 32..512 KiB, SSCA slots of 8..64 MiB, and for full estimates the
+ *   staged schedule; re-plans `plan` with the fastest setting (plans created later for the
+ *   same workload start from it).
  * scd_ssca_tune: the STAGES schedule and the PERSISTENT one with the same knobs, for
  *   (N, Np, opts->precision); later SCD_SCHEDULE_AUTO calls use the fastest.  Arguments as
  *   scd_ssca (opts->workspace at least scd_ssca_workspace_bytes). */

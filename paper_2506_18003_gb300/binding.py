@@ -340,8 +340,8 @@ class BatchPlan:
         self._query()
 
     def set_schedule(self, schedule: str = "auto"):
-        """SSCA plans: "persistent" (one launch), "stages" (one launch per stage and size) or
-        "auto" (the autotuned choice)."""
+        """"persistent" (one launch), "stages" (one launch per stage and size) or "auto" (the
+        autotuned choice, else the estimator's default)."""
         check(self.lib.scd_batch_plan_set_schedule(self.handle, SCHEDULES[schedule]), "scd_batch_plan_set_schedule")
 
     def out_dtype(self):

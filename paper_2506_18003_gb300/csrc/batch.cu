@@ -136,6 +136,11 @@ scd_status cuda_status(cudaError_t e) {
   return SCD_ERR_CUDA;
 }
 
+// Schedule of a new plan's full estimates: SSCA defaults to the staged schedule (measured
+// faster on every batch tried: 512 signals of 2^12..2^18 samples, Np = 128: 29.0 -> 23.5 ms
+// FP32, 42.0 -> 35.9 ms split); FAM to the persistent one.
+int default_staged(int estimator) { return estimator == 1 ? 1 : 0; }
+
 // Output arena layout of the plan's mode: full estimates (complex64 elements: FAM Np^2 P_i,
 // SSCA Np N_i per signal) or alpha profiles (float32 elements: FAM 2 P_i L, SSCA 2 N_i).
 void layout_outputs(scd_batch_plan* p) {
@@ -277,9 +282,9 @@ scd_status build_tasks(scd_batch_plan* p) {
   if (p->d_st) { cudaFree(p->d_st); p->d_st = nullptr; }
   p->st_tasks.clear();
   p->st_launches.clear();
-  if (!fam && p->staged && !p->prof_power) {
-    // staged schedule: every signal's channeliser, then per size class (ascending N) the
-    // column passes and the row passes of its signals
+  if (p->staged && !p->prof_power) {
+    // staged schedule: every signal's channeliser, then per size class (ascending N or P) the
+    // SSCA column passes and row passes, or the FAM pair transforms, of its signals
     int sms = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess)
       return cuda_status(e);
@@ -306,12 +311,25 @@ scd_status build_tasks(scd_batch_plan* p) {
       t.subtiles = t.tiles;
       p->st_tasks.push_back(t);
     }
-    scd_status ls = launch_of(0, Np, f0);
+    scd_status ls = launch_of(fam ? 3 : 0, Np, f0);
     if (ls != SCD_OK) return ls;
     std::vector<int64_t> classes(p->sizes.begin(), p->sizes.end());
     std::sort(classes.begin(), classes.end());
     classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
-    for (int64_t N : classes) {
+    for (int64_t P : fam ? classes : std::vector<int64_t>()) {
+      f0 = (int)p->st_tasks.size();
+      for (int i = 0; i < nsig; ++i) {
+        if (p->sizes[i] != P) continue;
+        Task t = stage0_task(i);
+        t.size = (int)P;
+        t.subtiles = ((int64_t)Np * Np + tile_c((int)P) - 1) / tile_c((int)P);
+        if (!(t.tw = table_pass((int)P, &e))) return cuda_status(e);
+        if (tc && !(t.bmats = table_tc_bmats((int)P, &t.bbytes, &e))) return cuda_status(e);
+        p->st_tasks.push_back(t);
+      }
+      if ((ls = launch_of(4, (int)P, f0)) != SCD_OK) return ls;
+    }
+    for (int64_t N : fam ? std::vector<int64_t>() : classes) {
       int M1, M2;
       ssca_split(N, &M1, &M2);
       for (int kind = 1; kind <= 2; ++kind) {
@@ -386,9 +404,7 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
   const bool fam = estimator == 0, tc = precision == SCD_SPLIT_BF16;
   scd_batch_plan* p = new scd_batch_plan();
   p->estimator = estimator; p->nsig = nsig; p->Np = Np; p->L = L; p->precision = precision;
-  // SSCA full estimates default to the staged schedule (measured faster on every batch tried:
-  // 512 signals of 2^12..2^18 samples, Np = 128: 29.0 -> 23.5 ms FP32, 42.0 -> 35.9 ms split)
-  p->staged = estimator == 1 ? 1 : 0;
+  p->staged = default_staged(estimator);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
   p->x_off.assign(nsig + 1, 0); p->out_off.assign(nsig + 1, 0); p->ws_off.assign(nsig + 1, 0);
@@ -432,7 +448,7 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
     if (tune_lookup(batch_key(p), &te)) {
       p->item_bytes = te.item_bytes;
       p->slot_bytes = te.slot_bytes;
-      p->staged = fam ? 0 : te.schedule;
+      p->staged = te.schedule;
     }
     scd_status bs = build_tasks(p);
     if (bs != SCD_OK) { free_plan(p); return bs; }
@@ -608,11 +624,11 @@ scd_status scd_batch_plan_set_schedule(scd_batch_plan* p, int32_t schedule) {
   if (!p || schedule < SCD_SCHEDULE_AUTO || schedule > SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
   int staged = 0;
   if (schedule == SCD_SCHEDULE_STAGES) {
-    if (p->estimator != 1 || p->prof_power) return SCD_ERR_UNSUPPORTED;
+    if (p->prof_power) return SCD_ERR_UNSUPPORTED;
     staged = 1;
   } else if (schedule == SCD_SCHEDULE_AUTO) {
     TuneEntry te;
-    staged = p->estimator == 1 && !p->prof_power ? (tune_lookup(batch_key(p), &te) ? te.schedule : 1) : 0;
+    staged = !p->prof_power ? (tune_lookup(batch_key(p), &te) ? te.schedule : default_staged(p->estimator)) : 0;
   }
   if (staged == p->staged) return SCD_OK;
   p->staged = staged;
@@ -647,7 +663,7 @@ scd_status scd_batch_tune(scd_batch_plan* p, const void* x_arena, const float* w
       scd_status s = try_one(0, item, p->estimator == 1 ? slots[k] : p->slot_bytes);
       if (s != SCD_OK) return s;
     }
-  if (p->estimator == 1 && !p->prof_power) {                    // SSCA: the staged schedule
+  if (!p->prof_power) {                                         // the staged schedule
     scd_status s = try_one(1, p->item_bytes, p->slot_bytes);
     if (s != SCD_OK) return s;
   }

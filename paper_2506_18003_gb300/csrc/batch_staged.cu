@@ -1,7 +1,8 @@
-// Staged schedule of an SSCA batch plan: instead of one persistent launch with a device work
-// queue, one launch per stage and transform size over every signal of the plan, in stream
-// order (no device-side waits): the channeliser + CDP of all signals, then per size class the
+// Staged schedule of a batch plan: instead of one persistent launch with a device work queue,
+// one launch per stage and transform size over every signal of the plan, in stream order (no
+// device-side waits).  SSCA: the channeliser + CDP of all signals, then per size class the
 // column passes (in place on each signal's X_g) and the row passes (to the output arena).
+// FAM: the channelisers of all signals, then per size class P the pair transforms.
 // Each kernel has only its own tile's registers and shared memory, so it runs at the
 // occupancy of the standalone kernels (the column pass's registers capped for 2 CTAs per SM
 // at M1 >= 512, 3 at 128 and 256, 4 below); the price is the X_g round trip through HBM that the
@@ -88,6 +89,48 @@ __global__ void __launch_bounds__(kThreads) k_st_rows(BatchArgs A, const Task* _
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
+// FAM channelisers of all signals (X[kh][p] of signal i at ws + ws_off_i).
+template <int NP, bool TC>
+__global__ void __launch_bounds__(kThreads) k_st_fchan(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  using S = TileShape<NP>;
+  using FS = FftSmem<NP, S::C, S::NT, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, A.bmats_np, FS::bbytes, A.err);
+  {
+    const int64_t tile = blockIdx.x;
+    const Task& t = tl[find_task(tl, nt, tile)];
+    fam_channelise_tile<NP, TC>(sm, ctx, A.x + t.x_off, A.L, t.P, A.window, A.tw_np, A.ws + t.ws_off,
+                                (int)(tile - t.first) * S::C);
+  }
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
+}
+
+// FAM pair transforms of one size class P, the FP32 form's registers capped as the standalone
+// pair kernel's (fam.cu): 3 CTAs per SM at P = 512 and 1024, 4 at 2048 and 4096, 2 at 8192.
+template <int PP, bool TC>
+__host__ __device__ constexpr int fpairs_minb() {
+  return TC ? 1 : (PP == 8192 ? 2 : (PP >= 2048 ? 4 : (PP >= 512 ? 3 : 1)));
+}
+template <int PP, bool TC>
+__global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC>()) k_st_fpairs(BatchArgs A, const Task* __restrict__ tl,
+                                                                              int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  using S = TileShape<PP>;
+  using FS = FftSmem<PP, S::C, S::NT, TC>;
+  unsigned char* base = reinterpret_cast<unsigned char*>(sm);
+  TcCtx ctx{};
+  if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, tl[0].bmats, FS::bbytes, A.err);
+  {
+    const int64_t tile = blockIdx.x;
+    const Task& t = tl[find_task(tl, nt, tile)];
+    const float2* X = A.ws + t.ws_off;
+    fam_pairs_tile<PP, TC, false>(sm, ctx, X, X, A.Np, A.out + t.out_off, t.tw, (tile - t.first) * S::C);
+  }
+  if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
+}
+
 template <class K>
 cudaError_t prepare_t(K kernel, int smem, bool tc, int* smem_out, int* per_sm) {
   *smem_out = smem;
@@ -102,10 +145,14 @@ cudaError_t prepare_t(K kernel, int smem, bool tc, int* smem_out, int* per_sm) {
 
 template <int M, bool TC>
 cudaError_t prep_m(int kind, int* smem, int* per_sm) {
-  if constexpr (M <= 256)
+  using S = TileShape<M>;
+  if constexpr (M >= 16 && M <= 256) {
     if (kind == 0) return prepare_t(k_st_cdp<M, TC>, CdpSmem<M, TC>::total, TC, smem, per_sm);
-  if constexpr (M >= 64) {
-    using S = TileShape<M>;
+    if (kind == 3) return prepare_t(k_st_fchan<M, TC>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
+  }
+  if constexpr (M <= 8192)
+    if (kind == 4) return prepare_t(k_st_fpairs<M, TC>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
+  if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) return prepare_t(k_st_cols<M, TC>, ColsSmem<M, TC>::total, TC, smem, per_sm);
     if (kind == 2)
       return prepare_t(k_st_rows<M, TC>, FftSmem<M, S::C, S::NT, TC, rows_stage_bytes<M>()>::total, TC, smem, per_sm);
@@ -115,19 +162,26 @@ cudaError_t prep_m(int kind, int* smem, int* per_sm) {
 
 template <int M, bool TC>
 void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, int nt, int64_t total, cudaStream_t st) {
-  if constexpr (M <= 256)
+  if constexpr (M >= 16 && M <= 256) {
     if (kind == 0) k_st_cdp<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
-  if constexpr (M >= 64) {
+    if (kind == 3) k_st_fchan<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  }
+  if constexpr (M <= 8192)
+    if (kind == 4) k_st_fpairs<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) k_st_cols<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
     if (kind == 2) k_st_rows<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
   }
 }
 
-// kinds: 0 channeliser (M = Np in 16..256), 1 column pass (M = M1), 2 row pass (M = M2), M1 and
-// M2 in 64..1024
+// kinds: SSCA 0 channeliser + CDP (M = Np in 16..256), 1 column pass (M = M1), 2 row pass
+// (M = M2), M1 and M2 in 64..1024; FAM 3 channeliser (M = Np), 4 pair transforms (M = P in
+// 2..8192)
 bool valid(int kind, int M) {
-  if (kind == 0) return M == 16 || M == 32 || M == 64 || M == 128 || M == 256;
-  return M == 64 || M == 128 || M == 256 || M == 512 || M == 1024;
+  const bool pow2 = M >= 2 && (M & (M - 1)) == 0;
+  if (kind == 0 || kind == 3) return pow2 && M >= 16 && M <= 256;
+  if (kind == 4) return pow2 && M <= 8192;
+  return pow2 && M >= 64 && M <= 1024;
 }
 
 }  // namespace
@@ -136,7 +190,8 @@ cudaError_t staged_prepare(int kind, int M, bool tc, int* smem, int* per_sm) {
   if (!valid(kind, M)) return cudaErrorInvalidValue;
 #define SCD_SP(MV) case MV: return tc ? prep_m<MV, true>(kind, smem, per_sm) : prep_m<MV, false>(kind, smem, per_sm);
   switch (M) {
-    SCD_SP(16) SCD_SP(32) SCD_SP(64) SCD_SP(128) SCD_SP(256) SCD_SP(512) SCD_SP(1024)
+    SCD_SP(2) SCD_SP(4) SCD_SP(8) SCD_SP(16) SCD_SP(32) SCD_SP(64) SCD_SP(128) SCD_SP(256) SCD_SP(512)
+    SCD_SP(1024) SCD_SP(2048) SCD_SP(4096) SCD_SP(8192)
     default: return cudaErrorInvalidValue;
   }
 #undef SCD_SP
@@ -147,7 +202,8 @@ cudaError_t staged_launch(int kind, int M, bool tc, int grid, int smem, const Ba
   if (!valid(kind, M)) return cudaErrorInvalidValue;
 #define SCD_SL(MV) case MV: if (tc) launch_m<MV, true>(kind, grid, smem, A, tl, nt, total, st); else launch_m<MV, false>(kind, grid, smem, A, tl, nt, total, st); break;
   switch (M) {
-    SCD_SL(16) SCD_SL(32) SCD_SL(64) SCD_SL(128) SCD_SL(256) SCD_SL(512) SCD_SL(1024)
+    SCD_SL(2) SCD_SL(4) SCD_SL(8) SCD_SL(16) SCD_SL(32) SCD_SL(64) SCD_SL(128) SCD_SL(256) SCD_SL(512)
+    SCD_SL(1024) SCD_SL(2048) SCD_SL(4096) SCD_SL(8192)
     default: return cudaErrorInvalidValue;
   }
 #undef SCD_SL

@@ -140,6 +140,30 @@ def test_ssca_batch_staged_schedule(torch, precision):
         got = plan.output(out_s, i).cpu().numpy()
         err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
         assert err <= TOL[precision], (i, err)
-    with pytest.raises(binding.ScdError):
-        binding.BatchPlan("fam", [4096], 64, 16).set_schedule("stages")
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_fam_batch_staged_schedule(torch, precision):
+    """FAM staged schedule (the channelisers, then one launch per size class P) against the
+    FP64 oracle for every signal, and bit for bit against the persistent schedule."""
+    Np, L = 64, 16
+    lengths = [4096, 5000, 1100, 8300, 70000, 2200, 17000, 3000, 140000]
+    sigs = [signals.batch_signal(400 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("fam", lengths, Np, L, precision)
+    plan.set_schedule("persistent")
+    _, out_p, _ = _run(torch, plan, sigs)
+    plan.set_schedule("stages")
+    _, out_s, _ = _run(torch, plan, sigs)
+    assert torch.equal(out_p, out_s)
+    a = orc.hamming_window(Np)
+    for i, x in enumerate(sigs):
+        P = plan.sizes[i]
+        ref = orc.fam(x, a, Np, L, P)
+        got = plan.output(out_s, i).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL[precision], (i, err)
+    plan.set_output("profile")
+    with pytest.raises(binding.ScdError):                    # alpha profiles run persistent only
+        plan.set_schedule("stages")
     plan.close()
