@@ -209,7 +209,8 @@ class BatchWorkload:
         return {"workload": "batch: 512 signals, lengths log-uniform in [2^12, 2^18] (BPSK/QPSK/8PSK/16QAM/"
                             "AM-DSB/AWGN, sps {2,4,8,16}, fc U(+-0.25), SNR U[-5,15] dB); FAM Np=64 L=16 "
                             "(P_i = largest power of two that fits), SSCA Np=128 (N_i = largest power of two "
-                            "<= len_i); one persistent graph-captured launch per estimator",
+                            "<= len_i); one CUDA graph per estimator (persistent launch or staged launches, "
+                            "autotuned)",
                 "signals": len(self.lengths), "input_samples": int(sum(self.lengths)),
                 "fam": {"Np": self.FAM_NP, "L": self.FAM_L}, "ssca": {"Np": self.SSCA_NP},
                 "window": "hamming", "l2": "working set per step ~95 GB > L2 (no flush needed)"}
