@@ -237,8 +237,7 @@ SCD_API scd_status scd_batch_plan_set_output(scd_batch_plan* plan, int32_t mode)
  * channelisers, then per size class the SSCA column passes in place on the workspace and row
  * passes, or the FAM pair transforms; same workspace, no device-side waits);
  * SCD_SCHEDULE_AUTO = the autotuner's choice for this workload, else the default of new plans
- * (STAGES for SSCA, PERSISTENT for FAM).  Alpha-profile output always runs persistent
- * (STAGES: SCD_ERR_UNSUPPORTED). */
+ * (STAGES for SSCA, PERSISTENT for FAM).  Both schedules serve both output modes. */
 SCD_API scd_status scd_batch_plan_set_schedule(scd_batch_plan* plan, int32_t schedule);
 
 /* ------------------------------------------------------------------------------ streaming

@@ -282,7 +282,7 @@ scd_status build_tasks(scd_batch_plan* p) {
   if (p->d_st) { cudaFree(p->d_st); p->d_st = nullptr; }
   p->st_tasks.clear();
   p->st_launches.clear();
-  if (p->staged && !p->prof_power) {
+  if (p->staged) {
     // staged schedule: every signal's channeliser, then per size class (ascending N or P) the
     // SSCA column passes and row passes, or the FAM pair transforms, of its signals
     int sms = 0;
@@ -327,7 +327,7 @@ scd_status build_tasks(scd_batch_plan* p) {
         if (tc && !(t.bmats = table_tc_bmats((int)P, &t.bbytes, &e))) return cuda_status(e);
         p->st_tasks.push_back(t);
       }
-      if ((ls = launch_of(4, (int)P, f0)) != SCD_OK) return ls;
+      if ((ls = launch_of(p->prof_power ? 6 : 4, (int)P, f0)) != SCD_OK) return ls;
     }
     for (int64_t N : fam ? std::vector<int64_t>() : classes) {
       int M1, M2;
@@ -346,7 +346,7 @@ scd_status build_tasks(scd_batch_plan* p) {
           if (tc && !(t.bmats = table_tc_bmats(M, &t.bbytes, &e))) return cuda_status(e);
           p->st_tasks.push_back(t);
         }
-        if ((ls = launch_of(kind, M, f0)) != SCD_OK) return ls;
+        if ((ls = launch_of(kind == 2 && p->prof_power ? 5 : kind, M, f0)) != SCD_OK) return ls;
       }
     }
     if ((e = cudaMalloc(&p->d_st, sizeof(Task) * p->st_tasks.size())) != cudaSuccess ||
@@ -624,11 +624,10 @@ scd_status scd_batch_plan_set_schedule(scd_batch_plan* p, int32_t schedule) {
   if (!p || schedule < SCD_SCHEDULE_AUTO || schedule > SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
   int staged = 0;
   if (schedule == SCD_SCHEDULE_STAGES) {
-    if (p->prof_power) return SCD_ERR_UNSUPPORTED;
     staged = 1;
   } else if (schedule == SCD_SCHEDULE_AUTO) {
     TuneEntry te;
-    staged = !p->prof_power ? (tune_lookup(batch_key(p), &te) ? te.schedule : default_staged(p->estimator)) : 0;
+    staged = tune_lookup(batch_key(p), &te) ? te.schedule : default_staged(p->estimator);
   }
   if (staged == p->staged) return SCD_OK;
   p->staged = staged;
@@ -663,7 +662,7 @@ scd_status scd_batch_tune(scd_batch_plan* p, const void* x_arena, const float* w
       scd_status s = try_one(0, item, p->estimator == 1 ? slots[k] : p->slot_bytes);
       if (s != SCD_OK) return s;
     }
-  if (!p->prof_power) {                                         // the staged schedule
+  {                                                             // the staged schedule
     scd_status s = try_one(1, p->item_bytes, p->slot_bytes);
     if (s != SCD_OK) return s;
   }

@@ -274,9 +274,11 @@ cudaError_t prepare_kernel(bool fam, bool tc, bool prof, int smem, int* blocks_p
 cudaError_t launch_batch(bool fam, bool tc, bool prof, int grid, int smem, const BatchArgs& A, cudaStream_t st);
 cudaError_t prepare_kernel_profile(bool fam, bool tc, int smem, int* blocks_per_sm);
 cudaError_t launch_batch_profile(bool fam, bool tc, int grid, int smem, const BatchArgs& A, cudaStream_t st);
-// Staged SSCA schedule (batch_staged.cu): kind 0 channeliser + CDP (M = Np), 1 column pass
-// (M = M1), 2 row pass (M = M2), each over a task list whose tasks hold `first` and `subtiles`
-// in CTA tiles; a kind-1/2 list holds one size class.
+// Staged schedule (batch_staged.cu): kinds SSCA 0 channeliser + CDP (M = Np), 1 column pass
+// (M = M1), 2 row pass (M = M2); FAM 3 channeliser (M = Np), 4 pair transforms (M = P); 5 / 6
+// the row pass / pair transforms reducing into alpha profiles.  Each launch runs a task list
+// whose tasks hold `first` and `subtiles` in CTA tiles; lists of kinds 1, 2, 4, 5 and 6 hold one
+// size class.
 cudaError_t staged_prepare(int kind, int M, bool tc, int* smem, int* per_sm);
 cudaError_t staged_launch(int kind, int M, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl, int nt,
                           int64_t total, cudaStream_t st);

@@ -68,8 +68,9 @@ __global__ void __launch_bounds__(kThreads, M1 >= 512 ? 2 : (M1 >= 128 ? 3 : 4))
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-// Row passes of one size class.
-template <int M2, bool TC>
+// Row passes of one size class; PROF: each bin reduced into the signal's alpha profile
+// (out arena of float32 profiles) instead of stored.
+template <int M2, bool TC, bool PROF>
 __global__ void __launch_bounds__(kThreads) k_st_rows(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<M2>;
@@ -83,8 +84,16 @@ __global__ void __launch_bounds__(kThreads) k_st_rows(BatchArgs A, const Task* _
     const int64_t local = tile - t.first;
     const int per = t.M1 / S::C;
     const int64_t kh = local / per;
-    ssca_rows_tile<M2, TC>(sm, ctx, A.ws + t.ws_off + kh * t.N, A.out + t.out_off + kh * t.N, t.M1, t.tw,
-                           (int)(local % per) * S::C);
+    if constexpr (PROF) {
+      // alpha column of stored bin sh of channel k: ah = sh + k N/Np + N/2
+      const int ah_off = (int)(kh - A.Np / 2) * (t.N / A.Np) + t.N / 2;
+      ssca_rows_tile<M2, TC, false, true>(sm, ctx, A.ws + t.ws_off + kh * t.N, nullptr, t.M1, t.tw,
+                                          (int)(local % per) * S::C, reinterpret_cast<float*>(A.out) + t.out_off,
+                                          ah_off, A.prof_power);
+    } else {
+      ssca_rows_tile<M2, TC>(sm, ctx, A.ws + t.ws_off + kh * t.N, A.out + t.out_off + kh * t.N, t.M1, t.tw,
+                             (int)(local % per) * S::C);
+    }
   }
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
@@ -113,7 +122,7 @@ template <int PP, bool TC>
 __host__ __device__ constexpr int fpairs_minb() {
   return TC ? 1 : (PP == 8192 ? 2 : (PP >= 2048 ? 4 : (PP >= 512 ? 3 : 1)));
 }
-template <int PP, bool TC>
+template <int PP, bool TC, bool PROF>
 __global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC>()) k_st_fpairs(BatchArgs A, const Task* __restrict__ tl,
                                                                               int nt, int64_t total) {
   extern __shared__ __align__(128) float2 sm[];
@@ -126,7 +135,13 @@ __global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC>()) k_st_fpairs(B
     const int64_t tile = blockIdx.x;
     const Task& t = tl[find_task(tl, nt, tile)];
     const float2* X = A.ws + t.ws_off;
-    fam_pairs_tile<PP, TC, false>(sm, ctx, X, X, A.Np, A.out + t.out_off, t.tw, (tile - t.first) * S::C);
+    if constexpr (PROF) {
+      const int PL = t.P * A.L;
+      fam_pairs_tile<PP, TC, true>(sm, ctx, X, X, A.Np, nullptr, t.tw, (tile - t.first) * S::C,
+                                   reinterpret_cast<float*>(A.out) + t.out_off, PL, PL / A.Np, A.prof_power);
+    } else {
+      fam_pairs_tile<PP, TC, false>(sm, ctx, X, X, A.Np, A.out + t.out_off, t.tw, (tile - t.first) * S::C);
+    }
   }
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
@@ -150,12 +165,18 @@ cudaError_t prep_m(int kind, int* smem, int* per_sm) {
     if (kind == 0) return prepare_t(k_st_cdp<M, TC>, CdpSmem<M, TC>::total, TC, smem, per_sm);
     if (kind == 3) return prepare_t(k_st_fchan<M, TC>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
   }
-  if constexpr (M <= 8192)
-    if (kind == 4) return prepare_t(k_st_fpairs<M, TC>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
+  if constexpr (M <= 8192) {
+    if (kind == 4) return prepare_t(k_st_fpairs<M, TC, false>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
+    if (kind == 6) return prepare_t(k_st_fpairs<M, TC, true>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
+  }
   if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) return prepare_t(k_st_cols<M, TC>, ColsSmem<M, TC>::total, TC, smem, per_sm);
     if (kind == 2)
-      return prepare_t(k_st_rows<M, TC>, FftSmem<M, S::C, S::NT, TC, rows_stage_bytes<M>()>::total, TC, smem, per_sm);
+      return prepare_t(k_st_rows<M, TC, false>, FftSmem<M, S::C, S::NT, TC, rows_stage_bytes<M>()>::total, TC, smem,
+                       per_sm);
+    if (kind == 5)
+      return prepare_t(k_st_rows<M, TC, true>, FftSmem<M, S::C, S::NT, TC, rows_stage_bytes<M>()>::total, TC, smem,
+                       per_sm);
   }
   return cudaErrorInvalidValue;
 }
@@ -166,22 +187,25 @@ void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, 
     if (kind == 0) k_st_cdp<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
     if (kind == 3) k_st_fchan<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
   }
-  if constexpr (M <= 8192)
-    if (kind == 4) k_st_fpairs<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  if constexpr (M <= 8192) {
+    if (kind == 4) k_st_fpairs<M, TC, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    if (kind == 6) k_st_fpairs<M, TC, true><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  }
   if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) k_st_cols<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
-    if (kind == 2) k_st_rows<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    if (kind == 2) k_st_rows<M, TC, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    if (kind == 5) k_st_rows<M, TC, true><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
   }
 }
 
 // kinds: SSCA 0 channeliser + CDP (M = Np in 16..256), 1 column pass (M = M1), 2 row pass
 // (M = M2), M1 and M2 in 64..1024; FAM 3 channeliser (M = Np), 4 pair transforms (M = P in
-// 2..8192)
+// 2..8192); 5 and 6: kinds 2 and 4 reducing into alpha profiles
 bool valid(int kind, int M) {
   const bool pow2 = M >= 2 && (M & (M - 1)) == 0;
   if (kind == 0 || kind == 3) return pow2 && M >= 16 && M <= 256;
-  if (kind == 4) return pow2 && M <= 8192;
-  return pow2 && M >= 64 && M <= 1024;
+  if (kind == 4 || kind == 6) return pow2 && M <= 8192;
+  return pow2 && M >= 64 && M <= 1024 && kind >= 1 && kind <= 5;
 }
 
 }  // namespace

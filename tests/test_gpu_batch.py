@@ -163,7 +163,26 @@ def test_fam_batch_staged_schedule(torch, precision):
         got = plan.output(out_s, i).cpu().numpy()
         err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
         assert err <= TOL[precision], (i, err)
+    plan.close()
+
+
+@pytest.mark.parametrize("estimator,Np,L", [("fam", 64, 16), ("ssca", 64, 1)])
+def test_batch_profile_output_both_schedules(torch, estimator, Np, L):
+    """Alpha-profile output: the staged schedule's profiles equal the persistent schedule's bit
+    for bit (maxima do not depend on the order of the reductions)."""
+    lengths = [4096, 70000, 9000, 33000]
+    sigs = [signals.batch_signal(500 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan(estimator, lengths, Np, L)
     plan.set_output("profile")
-    with pytest.raises(binding.ScdError):                    # alpha profiles run persistent only
-        plan.set_schedule("stages")
+    x = _arena(torch, sigs)
+    ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
+    outs = []
+    for sched in ("persistent", "stages"):
+        plan.set_schedule(sched)
+        out = torch.empty(plan.out_offsets[-1], dtype=torch.float32, device="cuda")
+        plan.run(x, out, ws)
+        binding.scd_check_device()
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
+    assert float(outs[1].max()) > 0
     plan.close()
