@@ -1,5 +1,6 @@
-// Batched form: hundreds of signals of uneven lengths through ONE persistent launch per
-// estimator, captured in a CUDA graph.
+// Batched form: hundreds of signals of uneven lengths through one CUDA graph per estimator,
+// holding either ONE persistent launch (below) or the staged schedule's launches (one per
+// stage and size class, batch_staged.cu; the SSCA default).
 //
 // A batch plan lists tasks (one stage of one signal: FAM channeliser / pair FFT, SSCA
 // channeliser+CDP / column pass / row pass), each a range of tiles (one tile = one CTA's
