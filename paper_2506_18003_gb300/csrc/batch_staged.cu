@@ -29,7 +29,7 @@ __device__ __forceinline__ int find_task(const Task* __restrict__ tl, int nt, in
 }
 
 template <int NP, bool TC>
-__global__ void __launch_bounds__(kThreads) k_st_cdp(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+__device__ __forceinline__ void st_cdp_cta(const BatchArgs& A, const Task* __restrict__ tl, int nt) {
   extern __shared__ __align__(128) float2 sm[];
   using FS = CdpSmem<NP, TC>;
   static_assert(TileShape<NP>::NT == kThreads, "one tile per CTA");
@@ -45,6 +45,20 @@ __global__ void __launch_bounds__(kThreads) k_st_cdp(BatchArgs A, const Task* __
   }
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
+
+template <int NP, bool TC>
+__global__ void __launch_bounds__(kThreads) k_st_cdp(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  st_cdp_cta<NP, TC>(A, tl, nt);
+}
+
+// The FP32 channeliser at Np >= 64 held to 48 registers: five CTAs per SM, as its shared memory
+// allows (batch SSCA 23.42 -> 23.12 ms; the split form lost under any cap).
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 5) k_st_cdp5(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  st_cdp_cta<NP, false>(A, tl, nt);
+}
+template <int NP, bool TC>
+constexpr bool cdp_capped() { return !TC && NP >= 64; }
 
 // Column passes of one size class (all tasks share N, M1, M2 and the tables).
 template <int M1, bool TC>
@@ -162,7 +176,10 @@ template <int M, bool TC>
 cudaError_t prep_m(int kind, int* smem, int* per_sm) {
   using S = TileShape<M>;
   if constexpr (M >= 16 && M <= 256) {
-    if (kind == 0) return prepare_t(k_st_cdp<M, TC>, CdpSmem<M, TC>::total, TC, smem, per_sm);
+    if (kind == 0) {
+      if constexpr (cdp_capped<M, TC>()) return prepare_t(k_st_cdp5<M>, CdpSmem<M, TC>::total, TC, smem, per_sm);
+      else return prepare_t(k_st_cdp<M, TC>, CdpSmem<M, TC>::total, TC, smem, per_sm);
+    }
     if (kind == 3) return prepare_t(k_st_fchan<M, TC>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
   }
   if constexpr (M <= 8192) {
@@ -184,7 +201,10 @@ cudaError_t prep_m(int kind, int* smem, int* per_sm) {
 template <int M, bool TC>
 void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, int nt, int64_t total, cudaStream_t st) {
   if constexpr (M >= 16 && M <= 256) {
-    if (kind == 0) k_st_cdp<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    if (kind == 0) {
+      if constexpr (cdp_capped<M, TC>()) k_st_cdp5<M><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+      else k_st_cdp<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    }
     if (kind == 3) k_st_fchan<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
   }
   if constexpr (M <= 8192) {
