@@ -204,6 +204,18 @@ SCD_API scd_status scd_ssca_alpha_profile(const void* S, int64_t N, int32_t Np, 
 typedef struct scd_batch_plan scd_batch_plan;
 SCD_API scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np,
                                          int32_t L, int32_t precision, scd_batch_plan** out);
+/* Exact-length plan: no sample is dropped.  Per-signal sizes FAM P_i = floor((len_i - Np)/L) + 1
+ * (>= 2; at most 8192 unless a power of two <= 16384) and SSCA N_i = len_i (>= 4096; at most 2^19
+ * unless a power of two <= 2^20); sizes that are not powers of two run by Bluestein's identity
+ * (as scd_fam / scd_ssca).  scd_batch_run then runs each signal's estimate with the
+ * single-estimate kernels, one signal after the other on the stream (plain launches, no graph;
+ * the workspace is the largest single estimate's, from scd_batch_query).  Full estimates only:
+ * scd_batch_plan_set_output(plan, 1 or 2) and scd_batch_plan_set_schedule(plan, STAGES or
+ * PERSISTENT) give SCD_ERR_UNSUPPORTED; scd_batch_tune runs once.  The tables of every size
+ * are built here, so runs allocate nothing.  Errors as scd_batch_plan_create, and
+ * SCD_ERR_UNSUPPORTED for sizes outside the limits above. */
+SCD_API scd_status scd_batch_plan_create_exact(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np,
+                                               int32_t L, int32_t precision, scd_batch_plan** out);
 /* Layout of the arenas (any output pointer may be NULL):
  *   x_offsets[nsig+1]    signal i starts at x_arena[x_offsets[i]] (batches: it is
  *                        x_arena[x_offsets[i] .. x_offsets[i+1]); streaming windows overlap);

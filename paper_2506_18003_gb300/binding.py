@@ -61,6 +61,8 @@ SIGNATURES = {
     "scd_batch_plan_destroy": (None, [_vp]),
     "scd_batch_plan_set_output": (_i32, [_vp, _i32]),
     "scd_batch_plan_set_schedule": (_i32, [_vp, _i32]),
+    "scd_batch_plan_create_exact": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_int64), _i32, _i32, _i32,
+                                           ctypes.POINTER(_vp)]),
     "scd_batch_tune": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "scd_stream_plan_create": (_i32, [_i32, _i64, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_void_p)]),
     "scd_stream_advance": (_i32, [_vp, _vp, _vp, _i32, _vp]),
@@ -315,7 +317,9 @@ class BatchPlan:
     estimator: "fam" or "ssca"; lengths: signal lengths; the arenas are torch tensors:
     x_arena complex64[x_offsets[-1]], out_arena complex64[out_offsets[-1]]."""
 
-    def __init__(self, estimator: str, lengths, Np: int, L: int = 1, precision="fp32"):
+    def __init__(self, estimator: str, lengths, Np: int, L: int = 1, precision="fp32", exact=False):
+        """exact: every sample used (scd_batch_plan_create_exact: FAM P_i = (len_i - Np)//L + 1,
+        SSCA N_i = len_i, not rounded down to powers of two)."""
         lib = load()
         self.lib = lib
         self.estimator = estimator
@@ -324,8 +328,9 @@ class BatchPlan:
         arr = (ctypes.c_int64 * self.nsig)(*[int(v) for v in lengths])
         handle = ctypes.c_void_p()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        check(lib.scd_batch_plan_create({"fam": 0, "ssca": 1}[estimator], self.nsig, arr, Np, L, prec,
-                                        ctypes.byref(handle)), "scd_batch_plan_create")
+        create = lib.scd_batch_plan_create_exact if exact else lib.scd_batch_plan_create
+        check(create({"fam": 0, "ssca": 1}[estimator], self.nsig, arr, Np, L, prec, ctypes.byref(handle)),
+              "scd_batch_plan_create_exact" if exact else "scd_batch_plan_create")
         self.handle = handle
         self._query()
 

@@ -85,7 +85,8 @@ struct scd_batch_plan {
   int estimator = 0, nsig = 0, Np = 0, L = 0, precision = 0, device = 0;
   int64_t item_bytes = scd::bk::kItemBytes;   // tunables (autotuner): output bytes per queue item,
   int64_t slot_bytes = scd::bk::kSlotBytes;   // bytes of one SSCA column-pass slot
-  int staged = 0;                         // SSCA: 1 = staged schedule (batch_staged.cu)
+  int staged = 0;                         // 1 = staged schedule (batch_staged.cu)
+  int exact = 0;                          // 1 = exact-length plan: every sample, per-signal launches
   uint64_t signature = 0;                 // hash of (estimator, Np, L, precision, lengths)
   std::vector<int64_t> x_off, out_off, ws_off, sizes, used;
   std::vector<scd::bk::Task> tasks;
@@ -474,9 +475,93 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
   *out = p;
   return SCD_OK;
 }
+// Exact-length plan: every signal's estimate at the sizes its length gives (FAM P_i =
+// floor((len_i - Np)/L) + 1, SSCA N_i = len_i), run with the single-estimate kernels (Bluestein's
+// identity for the sizes that are not powers of two) one signal after the other on the stream.
+scd_status plan_create_exact(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np, int32_t L,
+                             int32_t precision, scd_batch_plan** out) {
+  using namespace scd;
+  if (!out || !lengths || nsig < 1 || (estimator != 0 && estimator != 1)) return SCD_ERR_ARG;
+  *out = nullptr;
+  if (Np < 16 || Np > 256 || !is_pow2(Np)) return SCD_ERR_UNSUPPORTED;
+  if (estimator == 0 && L < 1) return SCD_ERR_ARG;
+  if (precision != SCD_FP32 && precision != SCD_SPLIT_BF16) return SCD_ERR_UNSUPPORTED;
+  const bool fam = estimator == 0;
+  scd_batch_plan* p = new scd_batch_plan();
+  p->estimator = estimator; p->nsig = nsig; p->Np = Np; p->L = L; p->precision = precision;
+  p->exact = 1;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
+  p->x_off.assign(nsig + 1, 0); p->out_off.assign(nsig + 1, 0); p->ws_off.assign(nsig + 1, 0);
+  p->sizes.assign(nsig, 0); p->used.assign(nsig, 0);
+  size_t ws = 0;
+  for (int i = 0; i < nsig; ++i) {
+    const int64_t len = lengths[i];
+    if (len < 1) { free_plan(p); return SCD_ERR_ARG; }
+    int64_t sz;
+    if (fam) {
+      if (len < Np + L) { free_plan(p); return SCD_ERR_ARG; }   // at least two blocks
+      sz = (len - Np) / L + 1;
+      if (sz > 16384 || (!is_pow2(sz) && sz > 8192)) { free_plan(p); return SCD_ERR_UNSUPPORTED; }
+      p->used[i] = (sz - 1) * L + Np;
+      ws = std::max(ws, scd_fam_workspace_bytes(p->used[i], Np, L, (int32_t)sz, precision));
+    } else {
+      sz = len;
+      if (sz < 4096) { free_plan(p); return SCD_ERR_ARG; }
+      if (sz > (1 << 20) || (!is_pow2(sz) && sz > (1 << 19))) { free_plan(p); return SCD_ERR_UNSUPPORTED; }
+      p->used[i] = sz;
+      ws = std::max(ws, is_pow2(sz) ? sizeof(float2) * (size_t)Np * sz : ssca_any_workspace(sz, Np));
+    }
+    p->sizes[i] = sz;
+    p->x_off[i + 1] = p->x_off[i] + len;
+    // the tables of this size, built now (runs then allocate nothing)
+    const scd_status ps = scd_prepare(estimator, sz, Np, fam ? (int32_t)sz : 0);
+    if (ps != SCD_OK) { free_plan(p); return ps; }
+  }
+  layout_outputs(p);
+  p->ws_bytes = ws;
+  if (!(p->hamming = table_hamming(Np, &e)) || !(p->err = device_error_word(&e))) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  *out = p;
+  return SCD_OK;
+}
+
+// One exact-length run: per signal, the single-estimate stages on the shared workspace.
+cudaError_t run_exact(const scd_batch_plan* p, const float2* x, const float* w, float2* out, void* ws,
+                      cudaStream_t st) {
+  using namespace scd;
+  const int Np = p->Np, prec = p->precision;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < p->nsig && e == cudaSuccess; ++i) {
+    const float2* xi = x + p->x_off[i];
+    float2* oi = out + p->out_off[i];
+    const int64_t sz = p->sizes[i];
+    if (p->estimator == 0) {
+      float2* X = (float2*)ws;
+      if ((e = fam_channelise(xi, Np, p->L, (int)sz, w, X, st, prec)) != cudaSuccess) break;
+      e = is_pow2(sz) ? fam_pair_fft(X, X, Np, (int)sz, oi, st, prec) : fam_pair_fft_any(X, X, Np, (int)sz, oi, st, prec);
+    } else if (is_pow2(sz)) {
+      if ((e = ssca_cdp(xi, xi, false, sz, Np, w, (float2*)ws, st, prec)) != cudaSuccess) break;
+      if ((e = ssca_cols((float2*)ws, sz, Np, st, prec)) != cudaSuccess) break;
+      e = ssca_rows((const float2*)ws, sz, Np, oi, st, prec);
+    } else {
+      if ((e = ssca_any_cdp(xi, xi, false, sz, Np, w, ws, st, prec)) != cudaSuccess) break;
+      if ((e = ssca_any_first(sz, Np, ws, st, prec)) != cudaSuccess) break;
+      e = ssca_any_second(sz, Np, ws, oi, st, prec);
+    }
+  }
+  return e;
+}
 }  // namespace
 
 extern "C" {
+
+scd_status scd_batch_plan_create_exact(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np,
+                                       int32_t L, int32_t precision, scd_batch_plan** out) {
+  return plan_create_exact(estimator, nsig, lengths, Np, L, precision, out);
+}
 
 scd_status scd_batch_plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, int32_t Np, int32_t L,
                                  int32_t precision, scd_batch_plan** out) {
@@ -546,6 +631,10 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   if (dev != p->device) return SCD_ERR_ARG;
   const float* w = window ? window : p->hamming;
   cudaStream_t st = (cudaStream_t)stream;
+  if (p->exact) {                                               // plain launches, no graph
+    e = run_exact(p, (const float2*)x_arena, w, (float2*)out_arena, workspace, st);
+    return e == cudaSuccess ? SCD_OK : cuda_status(e);
+  }
   BatchArgs A;
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = p->Np; A.L = p->L; A.total = p->total;
   A.counters = p->d_counters; A.x = (const float2*)x_arena; A.y = A.x; A.conj = 0; A.pad_ = 0;
@@ -600,6 +689,7 @@ void scd_batch_plan_destroy(scd_batch_plan* p) { free_plan(p); }
 scd_status scd_batch_plan_set_output(scd_batch_plan* p, int32_t mode) {
   using namespace scd;
   if (!p || mode < 0 || mode > 2) return SCD_ERR_ARG;
+  if (p->exact) return mode ? SCD_ERR_UNSUPPORTED : SCD_OK;
   const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
   if (mode && fam) {                                            // the FAM map's band must tile alpha
     if (2 * (int64_t)p->L > p->Np) return SCD_ERR_UNSUPPORTED;
@@ -623,6 +713,7 @@ scd_status scd_batch_plan_set_output(scd_batch_plan* p, int32_t mode) {
 scd_status scd_batch_plan_set_schedule(scd_batch_plan* p, int32_t schedule) {
   using namespace scd;
   if (!p || schedule < SCD_SCHEDULE_AUTO || schedule > SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
+  if (p->exact) return schedule == SCD_SCHEDULE_AUTO ? SCD_OK : SCD_ERR_UNSUPPORTED;
   int staged = 0;
   if (schedule == SCD_SCHEDULE_STAGES) {
     staged = 1;
@@ -639,6 +730,12 @@ scd_status scd_batch_tune(scd_batch_plan* p, const void* x_arena, const float* w
                           void* workspace, void* stream, int32_t reps) {
   using namespace scd;
   if (!p || reps < 1) return SCD_ERR_ARG;
+  if (p->exact) {                                               // nothing to tune: one run
+    scd_status s = scd_batch_run(p, x_arena, window, out_arena, workspace, stream);
+    if (s != SCD_OK) return s;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    return e == cudaSuccess ? SCD_OK : cuda_status(e);
+  }
   const int64_t items[] = {32ll << 10, 64ll << 10, 128ll << 10, 256ll << 10, 512ll << 10};
   const int64_t slots[] = {8ll << 20, 16ll << 20, 32ll << 20, 64ll << 20};
   const int nslots = p->estimator == 0 ? 1 : 4;

@@ -208,3 +208,15 @@ def test_normalise_validation(lib):
     assert lib.scd_ssca(FAKE, 4096, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_UNSUPPORTED
     o.y = None
     assert lib.scd_fam_noalloc(FAKE, 280, 32, 8, 32, None, FAKE, ctypes.byref(o)) == binding.SCD_ERR_UNSUPPORTED
+
+
+def test_exact_plan_validation(lib):
+    """Exact-length plans reject bad arguments before touching a device."""
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 2)(5000, 6000)
+    assert lib.scd_batch_plan_create_exact(1, 0, arr, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
+    assert lib.scd_batch_plan_create_exact(2, 2, arr, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
+    assert lib.scd_batch_plan_create_exact(1, 2, arr, 24, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_UNSUPPORTED
+    assert lib.scd_batch_plan_create_exact(0, 2, arr, 32, 0, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
+    assert lib.scd_batch_plan_create_exact(1, 2, arr, 32, 1, 7, ctypes.byref(h)) == binding.SCD_ERR_UNSUPPORTED
+    assert lib.scd_batch_plan_create_exact(1, 2, None, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG

@@ -186,3 +186,43 @@ def test_batch_profile_output_both_schedules(torch, estimator, Np, L):
     assert torch.equal(outs[0], outs[1])
     assert float(outs[1].max()) > 0
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_fam_batch_exact_lengths(torch, precision):
+    """Exact-length FAM plan: P_i = (len_i - Np)//L + 1 (powers of two and not), every signal
+    against the FP64 oracle."""
+    Np, L = 32, 8
+    lengths = [1000, 1048, 824, 2000, 300]
+    sigs = [signals.batch_signal(600 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("fam", lengths, Np, L, precision, exact=True)
+    assert plan.sizes == [(n - Np) // L + 1 for n in lengths]
+    _, out, _ = _run(torch, plan, sigs)
+    a = orc.hamming_window(Np)
+    for i, x in enumerate(sigs):
+        ref = orc.fam(x, a, Np, L, plan.sizes[i])
+        got = plan.output(out, i).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL[precision], (i, err)
+    with pytest.raises(binding.ScdError):
+        plan.set_output("profile")
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_ssca_batch_exact_lengths(torch, precision):
+    """Exact-length SSCA plan: N_i = len_i (powers of two and not), every signal against the
+    FP64 oracle."""
+    Np = 32
+    lengths = [5000, 8192, 4500, 12289]
+    sigs = [signals.batch_signal(700 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("ssca", lengths, Np, 1, precision, exact=True)
+    assert plan.sizes == lengths
+    _, out, _ = _run(torch, plan, sigs)
+    a = orc.hamming_window(Np)
+    for i, x in enumerate(sigs):
+        ref = orc.ssca(x, a, Np)
+        got = plan.output(out, i).cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        assert err <= TOL[precision], (i, err)
+    plan.close()
