@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) k_st_cdp(BatchArgs A, const Task* __
 }
 
 // The FP32 channeliser at Np >= 64 held to 48 registers: five CTAs per SM, as its shared memory
-// allows (batch SSCA 23.42 -> 23.12 ms; the split form lost under any cap).
+// allows (batch SSCA 23.42 -> 23.12 ms; the split form, capped for three, lost 35.8 -> 37.2 ms).
 template <int NP>
 __global__ void __launch_bounds__(kThreads, 5) k_st_cdp5(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
   st_cdp_cta<NP, false>(A, tl, nt);
