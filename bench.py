@@ -632,6 +632,46 @@ def strip_fft_rates(binding, lib, stream, xs, Ss, work, hbm, reps):
     return res
 
 
+def paper_match(torch, binding, dev, stream, reps):
+    """The paper's own configurations (Sec. IV) on DSSS BPSK at 10 dB: FAM N=2048 (zero-padded to
+    (P-1)L+Np = 2240), Np=256, L=64, P=32; SSCA N=2^20, Np=64.  Per call, CUDA events around
+    `reps` calls after 2 warm-ups, FP32; the paper's VCK5000 times beside them as context only."""
+    from paper_2506_18003_gb300 import signals
+    res = {}
+    Np, L, P = 256, 64, 32
+    xf = torch.zeros((P - 1) * L + Np, dtype=torch.complex64, device=dev)
+    xf[:2048] = torch.from_numpy(signals.dsss_bpsk(2048, 10.0, seed=9400)).to(dev)
+    Sf = torch.empty((Np, Np, P), dtype=torch.complex64, device=dev)
+    xs = torch.from_numpy(signals.dsss_bpsk(1 << 20, 10.0, seed=9401)).to(dev)
+    Ss = torch.empty((64, 1 << 20), dtype=torch.complex64, device=dev)
+    lib = binding.load()
+    work = torch.empty(max(lib.scd_fam_workspace_bytes(xf.numel(), Np, L, P, 0),
+                           lib.scd_ssca_workspace_bytes(1 << 20, 64, 0)), dtype=torch.uint8, device=dev)
+    cases = {"fam": (lambda: binding.scd_fam(xf, Np, L, P, out=Sf, stream=stream, workspace=work), 2048, Np * Np * P,
+                     0.630),
+             "ssca": (lambda: binding.scd_ssca(xs, 64, out=Ss, stream=stream, workspace=work), 1 << 20, 64 << 20,
+                      114.0)}
+    with torch.cuda.stream(stream):
+        for name, (fn, samples, points, paper_ms) in cases.items():
+            for _ in range(2):
+                fn()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                fn()
+            t1.record(stream)
+            t1.synchronize()
+            ms = t0.elapsed_time(t1) / reps
+            res[name] = {"ms": round(ms, 5), "msamples_per_s": round(samples / (ms * 1e-3) / 1e6, 2),
+                         "scd_points_per_s": round(points / (ms * 1e-3), 0),
+                         "context_paper_vck5000_ms": paper_ms}
+    binding.scd_check_device(stream)
+    del Sf, Ss, work
+    torch.cuda.empty_cache()
+    res["config"] = "FAM N=2048 (zero-padded to 2240) Np=256 L=64 P=32; SSCA N=2^20 Np=64; DSSS BPSK 10 dB; FP32"
+    return res
+
+
 def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
     """Times the cross / conjugate estimates and the alpha profiles at the paper-scale sizes
     (FAM N=65,728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256), outside the step's timed region:
@@ -700,6 +740,7 @@ def measure_variants(torch, binding, dev, stream, reps=10, warmup=2):
     binding.scd_check_device(stream)
     del Sf, Ss, work
     torch.cuda.empty_cache()
+    out["paper_match"] = paper_match(torch, binding, dev, stream, reps)
     out["sizes"] = ("FAM N=65728 Np=256 L=64 P=1024; SSCA N=2^20 Np=256; any-length: FAM P=1000 (N=64,192), "
                     "SSCA N=500,000 (Bluestein, cyclic length 2^20); FP32 form; %d calls each" % reps)
     # streaming: one group of windows per step, new samples copied in from pinned host memory

@@ -221,3 +221,16 @@ def test_ssca_2p19_both_schedules(torch, schedule, precision):
     assert float(np.max(np.abs(got - ref))) / smax <= tol
     del got_t
     torch.cuda.empty_cache()
+
+
+def test_fam_paper_match_dsss(torch):
+    """The paper's own FAM configuration (Sec. IV: N = 2048 samples of DSSS BPSK at 10 dB,
+    Np = 256, L = 64, P = 32; the 2048 samples zero-padded to (P - 1) L + Np = 2240): every
+    cell against the oracle."""
+    Np, L, P = 256, 64, 32
+    x = np.zeros((P - 1) * L + Np, dtype=np.complex64)
+    x[:2048] = signals.dsss_bpsk(2048, 10.0, seed=9400)
+    a = orc.hamming_window(Np)
+    got = binding.scd_fam(_dev(torch, x), Np, L, P, window=_dev(torch, a)).cpu().numpy()
+    ref = orc.fam(x, a, Np, L, P)
+    assert _rel(got, ref) <= FP32_TOL
