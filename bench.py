@@ -867,6 +867,10 @@ def run_ours(args):
                 "frac": ach_gbs / hbm, "peak_source": peak_src, "algorithmic_bytes": kb[top],
                 "alu_frac": ach_tf / alu_peak, "algorithmic_flops": kf[top]}
     roof["traffic"] = captured_traffic(top) if prec == "fp32" else None
+    if roof["traffic"]:
+        # the captured DRAM bytes at the live stage time, against the copy bandwidth: how close
+        # the stage runs to HBM on the traffic it really moves
+        roof["traffic_hbm_frac"] = roof["traffic"] / (stage_ms[top] * 1e-3) / 1e9 / hbm
     value = job_throughput(world, wl.samples_per_step(), ms_step * 1e-3) / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
