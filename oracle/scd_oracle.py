@@ -30,7 +30,9 @@ Besides the auto estimate (the paper's case) both estimators take a second signa
 (the cross estimate of Sec. II-A, Eq. II.A-SCD function) and a conjugate form (the
 product without the conjugation); alpha profiles are the column maxima of the maps.
 
-Pins (tests/test_oracle_*.py): brute-force triple sums on tiny inputs (auto, cross and
+Pins (tests/test_oracle_*.py): the default symmetric Hamming window against scipy's
+hamming(sym=True) and its closed forms (0.08 endpoints, symmetry, peak, sum), the
+Dolph-Chebyshev window against scipy's chebwin, brute-force triple sums on tiny inputs (auto, cross and
 conjugate; power-of-two and other sizes, odd ones included), direct vs fft mode, cross Hermitian symmetry, the conjugate estimate as a
 cross estimate against conj(y) with the l axis reversed, the averaged-periodogram identity at alpha = 0 (also against scipy's Welch
 estimate), the lag-windowed correlogram at alpha = 0 for SSCA, exact conjugate
