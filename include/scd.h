@@ -320,15 +320,19 @@ SCD_API size_t scd_ssca_host_workspace_bytes(int64_t N, int32_t Np, int32_t prec
  * __device__ scratch array inside the library (about 2.25 MB, held by every GPU that loads
  * the library until the process exits), and calls no cudaMalloc, cudaFree or allocating
  * library routine.  Arguments, output and results are those of scd_fam (opts->workspace is
- * ignored), with one more limit: Np * P <= 262144 (e.g. Np = 256 with P <= 1024);
- * larger sizes return SCD_ERR_UNSUPPORTED and scd_last_error() names the limit.  Only the
- * auto estimate without normalisation: opts->y, opts->conjugate or opts->normalise set gives
- * SCD_ERR_UNSUPPORTED.
+ * ignored; the same argument checks), restricted to: the FP32 form (opts->precision =
+ * SCD_SPLIT_BF16 returns SCD_ERR_UNSUPPORTED); the auto estimate without normalisation
+ * (opts->y, opts->conjugate or opts->normalise set: SCD_ERR_UNSUPPORTED); no per-stage timing
+ * (opts->stage_events non-NULL: SCD_ERR_UNSUPPORTED); P a power of two; and Np * P <= 262144
+ * (e.g. Np = 256 with P <= 1024, Np = 16 with P <= 16384).  Every rejection sets the text of
+ * scd_last_error(); a size beyond the scratch names the limit.
  * All calls share the scratch array, which keeps the last call's contents (each call
- * rewrites everything it reads, so nothing has to start at zero); calls whose executions
- * overlap on the same GPU race on it and must be serialised by the caller.  The first call
- * on a device resolves the array's device address (a one-time set-up per device); make
- * that first call before any stream capture on that device. */
+ * rewrites everything it reads, so nothing has to start at zero).  Calls that overlap on the
+ * same device (on different streams, or from different host threads) race on that device's
+ * array and must be serialised by the caller; calls on different devices are independent.
+ * The first call in a device's context resolves the array's device address (a set-up step,
+ * cached per device and context); make that first call before any stream capture on that
+ * device, and again after a device reset (cudaDeviceReset), which creates a new context. */
 SCD_API scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P,
                                    const float* window, void* out, const scd_opts* opts);
 

@@ -78,6 +78,10 @@ bool variant_ok(const scd_opts& o) {
 
 namespace scd {
 void set_last_error(const char* msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+scd_status check_fam_args(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window,
+                          const void* out) {
+  return check_fam(x, N, Np, L, P, window, out);
+}
 }  // namespace scd
 
 extern "C" {

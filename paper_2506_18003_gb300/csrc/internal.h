@@ -142,6 +142,10 @@ struct NvtxRange {
 void count_launches(int n);
 // Sets the text scd_last_error() returns on this thread.
 void set_last_error(const char* msg);
+// scd_fam's argument checks (pointers, alignment, Np, P, N >= (P - 1) L + Np), shared by the
+// entry points that take scd_fam's arguments.
+scd_status check_fam_args(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window,
+                          const void* out);
 
 // ---------------------------------------------------------------- helpers
 inline bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }

@@ -13,14 +13,18 @@
 //    Np * P <= kNoallocMaxX (= 2^18, i.e. Np=256 with P<=1024, Np=64 with P<=4096, ...);
 //    larger sizes are rejected with SCD_ERR_UNSUPPORTED before anything is enqueued, and
 //    scd_last_error() then names the limit;
+//  * FP32 form, auto estimate only, no per-stage timing events;
 //  * every GPU that loads the library holds the array (about 2.25 MB) until the process exits;
 //  * all calls share the array and it keeps the last call's contents: each call rebuilds the
 //    tables it uses and overwrites every element of X it reads, so nothing needs to start at
-//    zero; calls whose executions overlap on the GPU (different streams, or devices sharing
-//    nothing but this code) race on the array on the same device and must be serialised;
-//  * the first call on a device resolves the array's device address with
-//    cudaGetSymbolAddress (a set-up step per device, guarded by a mutex); make that first
-//    call before any stream capture on that device.
+//    zero; calls that overlap on the same device (on different streams, or issued from
+//    different host threads) race on that device's array and must be serialised by the
+//    caller; calls on different devices are independent (each device has its own copy);
+//  * the first call in a device context resolves the array's device address with
+//    cudaGetSymbolAddress (a set-up step guarded by a mutex, cached per device and keyed by
+//    the context's ID, so that a context created again after cudaDeviceReset resolves it
+//    again); make that first call before any stream capture on that device, and again after
+//    a device reset.
 // It calls no cudaMalloc, cudaFree or allocating library routine.
 #include <stdio.h>
 
@@ -40,25 +44,67 @@ constexpr int64_t kScratchLen = kNoallocMaxX + kTabLen;     // float2 elements
 
 __device__ __align__(256) float2 g_noalloc_scratch[kScratchLen];
 
+// The current context's unique ID (driver API, reached through the runtime's entry-point
+// query so that the library needs no link to libcuda); 0 when it cannot be read.
+using CtxGetCurrentFn = int (*)(void** ctx);
+using CtxGetIdFn = int (*)(void* ctx, unsigned long long* id);
+
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  }
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
 std::mutex g_noalloc_mu;
 constexpr int kMaxDevices = 64;
-float2* g_noalloc_addr[kMaxDevices] = {};
+struct Resolved {
+  unsigned long long ctx_id;   // context the address belongs to (0: unknown, resolve every call)
+  float2* addr;
+};
+Resolved g_noalloc_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (resolved once per device).
+// Device address of the scratch array in the current device's context.
 cudaError_t scratch_address(float2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  Resolved& r = g_noalloc_addr[dev];
+  const unsigned long long id = current_context_id();
+  if (!r.addr || id == 0 || r.ctx_id != id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);       // also makes the primary context current
     if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = (float2*)p;
+    r.addr = (float2*)p;
+    r.ctx_id = current_context_id();
   }
-  *out = g_noalloc_addr[dev];
+  *out = r.addr;
   return cudaSuccess;
+}
+
+scd_status reject(scd_status s, const char* why) {
+  char msg[200];
+  snprintf(msg, sizeof msg, "scd_fam_noalloc: %s", why);
+  scd::set_last_error(msg);
+  return s;
 }
 
 }  // namespace
@@ -67,21 +113,19 @@ extern "C" {
 
 scd_status scd_fam_noalloc(const void* x, int64_t N, int32_t Np, int32_t L, int32_t P, const float* window,
                            void* out, const scd_opts* opts) {
-  if (!x || !out || ((uintptr_t)x % 8) || ((uintptr_t)out % 16) || (window && ((uintptr_t)window % 4)))
-    return SCD_ERR_ARG;
-  if (L < 1 || N < 1) return SCD_ERR_ARG;
-  if (Np < 16 || Np > 256 || !scd::is_pow2(Np) || P < 2 || P > 16384 || !scd::is_pow2(P))
-    return SCD_ERR_UNSUPPORTED;
-  if ((int64_t)(P - 1) * L + Np > N) return SCD_ERR_ARG;
+  scd_status s = scd::check_fam_args(x, N, Np, L, P, window, out);
+  if (s != SCD_OK) return reject(s, "arguments rejected by scd_fam's checks");
+  if (!scd::is_pow2(P)) return reject(SCD_ERR_UNSUPPORTED, "P must be a power of two");
   if ((int64_t)Np * P > kNoallocMaxX) {
     char msg[160];
-    snprintf(msg, sizeof msg, "scd_fam_noalloc: Np*P = %lld exceeds the fixed scratch limit of %lld",
-             (long long)Np * P, (long long)kNoallocMaxX);
-    scd::set_last_error(msg);
-    return SCD_ERR_UNSUPPORTED;
+    snprintf(msg, sizeof msg, "Np*P = %lld exceeds the fixed scratch limit of %lld", (long long)Np * P,
+             (long long)kNoallocMaxX);
+    return reject(SCD_ERR_UNSUPPORTED, msg);
   }
-  if (opts && opts->precision != SCD_FP32) return SCD_ERR_UNSUPPORTED;
-  if (opts && (opts->y || opts->conjugate || opts->normalise)) return SCD_ERR_UNSUPPORTED;   // plain auto estimate only
+  if (opts && opts->precision != SCD_FP32) return reject(SCD_ERR_UNSUPPORTED, "only the FP32 form (SCD_FP32)");
+  if (opts && (opts->y || opts->conjugate || opts->normalise))
+    return reject(SCD_ERR_UNSUPPORTED, "only the auto estimate without normalisation");
+  if (opts && opts->stage_events) return reject(SCD_ERR_UNSUPPORTED, "stage_events are not recorded");
   cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
   float2* base = nullptr;
   cudaError_t e = scratch_address(&base);

@@ -220,3 +220,17 @@ def test_exact_plan_validation(lib):
     assert lib.scd_batch_plan_create_exact(0, 2, arr, 32, 0, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
     assert lib.scd_batch_plan_create_exact(1, 2, arr, 32, 1, 7, ctypes.byref(h)) == binding.SCD_ERR_UNSUPPORTED
     assert lib.scd_batch_plan_create_exact(1, 2, None, 32, 1, 0, ctypes.byref(h)) == binding.SCD_ERR_ARG
+
+
+def test_noalloc_argument_validation(lib):
+    """scd_fam_noalloc applies scd_fam's checks, then its own limits; every rejection comes
+    before any CUDA call and leaves a message in scd_last_error()."""
+    assert lib.scd_fam_noalloc(FAKE, 279, 32, 8, 32, None, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_fam_noalloc(FAKE, 280, 24, 8, 32, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+    assert lib.scd_fam_noalloc(FAKE, 1 << 20, 32, 8, 100, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+    assert b"power of two" in lib.scd_last_error()
+    assert lib.scd_fam_noalloc(FAKE, 1 << 20, 256, 64, 2048, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+    assert b"scratch limit" in lib.scd_last_error()
+    assert lib.scd_fam_noalloc(FAKE, 1 << 20, 32, 8, 1 << 16, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+    # the check that scd_fam has and the first version of this entry point lacked
+    assert lib.scd_fam_noalloc(FAKE, 1 << 32, 16, 1 << 20, 4096, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
