@@ -59,9 +59,20 @@ typedef enum { SCD_FP32 = 0, SCD_SPLIT_BF16 = 1 } scd_precision;
  * PERSISTENT: one persistent launch that runs the channeliser + CDP and then the column and
  *   row passes channel group by channel group through small rotating slots (so each group's
  *   intermediate is read back from L2).
+ * FUSED: two kernels: the channeliser, the channel-data product and the strip transform's
+ *   first pass in one (the product X_g never leaves the chip), the second pass in the other.
+ *   Where its tiles do not fit the sizes (FP32 form; Np in {64, 128, 256}, N = M1 M2 with
+ *   M1 = 64 or 128, Np <= M2 <= 1024: e.g. N = 2^13..2^17 at Np = 128, 2^14..2^16 at
+ *   Np = 256), the call runs the STAGES kernels instead.
  * AUTO: the choice scd_ssca_tune measured fastest for (N, Np, precision) on this GPU model
- *   (in this process, or from the SCD_TUNE_CACHE file); STAGES if never tuned. */
-typedef enum { SCD_SCHEDULE_AUTO = 0, SCD_SCHEDULE_STAGES = 1, SCD_SCHEDULE_PERSISTENT = 2 } scd_schedule;
+ *   (in this process, or from the SCD_TUNE_CACHE file); if never tuned, FUSED where it fits,
+ *   else STAGES. */
+typedef enum {
+  SCD_SCHEDULE_AUTO = 0,
+  SCD_SCHEDULE_STAGES = 1,
+  SCD_SCHEDULE_PERSISTENT = 2,
+  SCD_SCHEDULE_FUSED = 3
+} scd_schedule;
 
 /* Options.  Pass NULL for defaults: legacy default stream, FP32, no workspace, |S|,
  * no stage events, auto estimate.  Zero-initialise the struct before filling it. */
@@ -76,8 +87,9 @@ typedef struct {
    * scd_events_create) is recorded on the stream just before the call's i-th kernel and
    * the next one after its last kernel.  scd_fam launches 2 kernels (channeliser, pair
    * FFT; 3 for a cross or conjugate estimate: channeliser of x, of y, pair FFT); scd_ssca 3
-   * with the STAGES schedule (channeliser + CDP, column pass, row pass) or 1 with PERSISTENT
-   * (AUTO resolves to one of the two); each map and profile 1. */
+   * with the STAGES schedule (channeliser + CDP, column pass, row pass), 2 with FUSED
+   * (channeliser + CDP + first pass, second pass) or 1 with PERSISTENT (AUTO resolves to
+   * one of these); each map and profile 1. */
   void** stage_events;
   int32_t n_stage_events;
   int32_t schedule;         /* scd_ssca only: scd_schedule */

@@ -141,7 +141,7 @@ def _need(t, dtype, numel, name):
         raise TypeError(f"{name} must be a contiguous {dtype} tensor of at least {numel} elements")
 
 
-SCHEDULES = {"auto": 0, "stages": 1, "persistent": 2}
+SCHEDULES = {"auto": 0, "stages": 1, "persistent": 2, "fused": 3}
 
 
 NORMALISE = {None: 0, "none": 0, "power": 1, "peak": 2}
@@ -345,8 +345,10 @@ class BatchPlan:
         self._query()
 
     def set_schedule(self, schedule: str = "auto"):
-        """"persistent" (one launch), "stages" (one launch per stage and size) or "auto" (the
-        autotuned choice, else the estimator's default)."""
+        """"persistent" (one launch), "stages" (one launch per stage and size), "fused" (SSCA,
+        FP32: the channeliser, channel-data product and first strip pass in one kernel per size
+        class, where its tiles fit) or "auto" (the autotuned choice, else the estimator's
+        default)."""
         check(self.lib.scd_batch_plan_set_schedule(self.handle, SCHEDULES[schedule]), "scd_batch_plan_set_schedule")
 
     def out_dtype(self):

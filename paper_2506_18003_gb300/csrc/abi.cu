@@ -182,7 +182,8 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   if (!scd::is_pow2(N)) {
     // any N: the strip transform on Bluestein's identity (staged kernels only)
     if (o.schedule == SCD_SCHEDULE_PERSISTENT) return SCD_ERR_UNSUPPORTED;
-    if (o.schedule != SCD_SCHEDULE_AUTO && o.schedule != SCD_SCHEDULE_STAGES) return SCD_ERR_ARG;
+    if (o.schedule != SCD_SCHEDULE_AUTO && o.schedule != SCD_SCHEDULE_STAGES && o.schedule != SCD_SCHEDULE_FUSED)
+      return SCD_ERR_ARG;
     StageMarks m{o, 4};
     if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
     if ((e = scd::ssca_any_cdp((const float2*)x, y, conj, N, Np, window, ws, st, o.precision)) != cudaSuccess)
@@ -196,7 +197,19 @@ scd_status scd_ssca(const void* x, int64_t N, int32_t Np, const float* window, v
   }
   scd::TuneEntry choice{o.schedule, 0, 0, 0.0};
   if (o.schedule == SCD_SCHEDULE_AUTO) choice = scd::ssca_auto_choice(N, Np, o.precision);
-  if (choice.schedule != SCD_SCHEDULE_STAGES && choice.schedule != SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
+  if (choice.schedule != SCD_SCHEDULE_STAGES && choice.schedule != SCD_SCHEDULE_PERSISTENT &&
+      choice.schedule != SCD_SCHEDULE_FUSED)
+    return SCD_ERR_ARG;
+  if (choice.schedule == SCD_SCHEDULE_FUSED && scd::ssca_fused_supported(N, Np, o.precision)) {
+    StageMarks m{o, 3};
+    if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = scd::ssca_fused_chancol((const float2*)x, y, conj, N, Np, window, ws, st)) != cudaSuccess)
+      return cuda_fail(e);
+    if ((e = m.mark(1, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = scd::ssca_fused_rows(ws, N, Np, (float2*)out, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = m.mark(2, st)) != cudaSuccess) return cuda_fail(e);
+    return SCD_OK;
+  }
   if (choice.schedule == SCD_SCHEDULE_PERSISTENT) {
     StageMarks m{o, 2};
     if ((e = m.mark(0, st)) != cudaSuccess) return cuda_fail(e);

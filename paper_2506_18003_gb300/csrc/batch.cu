@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "batch_kernel.cuh"
+#include "ssca_fused.cuh"
 
 namespace scd {
 namespace bk {
@@ -138,10 +139,13 @@ scd_status cuda_status(cudaError_t e) {
   return SCD_ERR_CUDA;
 }
 
-// Schedule of a new plan's full estimates: SSCA defaults to the staged schedule (measured
-// faster on every batch tried: 512 signals of 2^12..2^18 samples, Np = 128: 29.0 -> 23.5 ms
-// FP32, 42.0 -> 35.9 ms split); FAM to the persistent one.
-int default_staged(int estimator) { return estimator == 1 ? 1 : 0; }
+// Schedule of a new plan's full estimates (the plan's `staged`: 0 persistent, 1 staged, 2 staged
+// with the fused SSCA kernels where their tiles fit): SSCA defaults to the staged schedule
+// (measured faster on every batch tried: 512 signals of 2^12..2^18 samples, Np = 128: 29.0 ->
+// 23.5 ms FP32, 42.0 -> 35.9 ms split), fused in the FP32 form; FAM to the persistent one.
+int default_staged(int estimator, int precision) {
+  return estimator == 1 ? (precision == SCD_FP32 ? 2 : 1) : 0;
+}
 
 // Output arena layout of the plan's mode: full estimates (complex64 elements: FAM Np^2 P_i,
 // SSCA Np N_i per signal) or alpha profiles (float32 elements: FAM 2 P_i L, SSCA 2 N_i).
@@ -300,15 +304,20 @@ scd_status build_tasks(scd_batch_plan* p) {
       }
       L.total = tiles;
       int per_sm = 0;
-      cudaError_t ee = staged_prepare(kind, M, tc, &L.smem, &per_sm);
+      cudaError_t ee = staged_prepare(kind, M, Np, tc, &L.smem, &per_sm);
       if (ee != cudaSuccess) return cuda_status(ee);
       if (tiles >= (int64_t)0x7FFFFFFF) return SCD_ERR_UNSUPPORTED;
       L.grid = (int)tiles;                                      // one CTA per tile
       p->st_launches.push_back(L);
       return SCD_OK;
     };
+    // fused SSCA kernels (staged == 2, FP32 form) for the size classes their tiles fit
+    const bool fused = !fam && !tc && p->staged == 2;
+    auto fused_n = [&](int64_t N, FusedSplit* fs) { return fused && fused_split(N, Np, fs); };
     int f0 = 0;
     for (int i = 0; i < nsig; ++i) {
+      FusedSplit fs;
+      if (fused_n(p->sizes[i], &fs)) continue;                  // its channeliser runs inside tile A
       Task t = stage0_task(i);
       t.subtiles = t.tiles;
       p->st_tasks.push_back(t);
@@ -332,6 +341,26 @@ scd_status build_tasks(scd_batch_plan* p) {
       if ((ls = launch_of(p->prof_power ? 6 : 4, (int)P, f0)) != SCD_OK) return ls;
     }
     for (int64_t N : fam ? std::vector<int64_t>() : classes) {
+      FusedSplit fs;
+      if (fused_n(N, &fs)) {
+        // tile A (kind 7, clusters of fs.Q CTAs), then tile B (kind 8; 9 reduces into profiles)
+        for (int kind = 7; kind <= 8; ++kind) {
+          f0 = (int)p->st_tasks.size();
+          for (int i = 0; i < nsig; ++i) {
+            if (p->sizes[i] != N) continue;
+            Task t = stage0_task(i);
+            t.M1 = fs.M1; t.M2 = fs.M2;
+            t.size = kind == 7 ? fs.M1 : fs.M2;
+            t.subtiles = kind == 7 ? (int64_t)fs.M2 * fs.Q : (int64_t)Np * (fs.M1 / tile_c(fs.M2));
+            if (!(t.tw = table_pass(t.size, &e))) return cuda_status(e);
+            if (kind == 7 && !(t.wN = table_roots((int)N, &e))) return cuda_status(e);
+            p->st_tasks.push_back(t);
+          }
+          if ((ls = launch_of(kind == 8 && p->prof_power ? 9 : kind, kind == 7 ? (int)N : fs.M2, f0)) != SCD_OK)
+            return ls;
+        }
+        continue;
+      }
       int M1, M2;
       ssca_split(N, &M1, &M2);
       for (int kind = 1; kind <= 2; ++kind) {
@@ -406,7 +435,7 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
   const bool fam = estimator == 0, tc = precision == SCD_SPLIT_BF16;
   scd_batch_plan* p = new scd_batch_plan();
   p->estimator = estimator; p->nsig = nsig; p->Np = Np; p->L = L; p->precision = precision;
-  p->staged = default_staged(estimator);
+  p->staged = default_staged(estimator, precision);
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
   p->x_off.assign(nsig + 1, 0); p->out_off.assign(nsig + 1, 0); p->ws_off.assign(nsig + 1, 0);
@@ -651,7 +680,8 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   auto launch_all = [&]() -> cudaError_t {
     if (!staged) return launch_batch(fam, tc, prof, grid, p->smem, A, st);
     for (const auto& L : p->st_launches) {
-      cudaError_t el = staged_launch(L.kind, L.M, tc, L.grid, L.smem, A, p->d_st + L.first, L.count, L.total, st);
+      cudaError_t el =
+          staged_launch(L.kind, L.M, p->Np, tc, L.grid, L.smem, A, p->d_st + L.first, L.count, L.total, st);
       if (el != cudaSuccess) return el;
     }
     return cudaSuccess;
@@ -712,14 +742,16 @@ scd_status scd_batch_plan_set_output(scd_batch_plan* p, int32_t mode) {
 
 scd_status scd_batch_plan_set_schedule(scd_batch_plan* p, int32_t schedule) {
   using namespace scd;
-  if (!p || schedule < SCD_SCHEDULE_AUTO || schedule > SCD_SCHEDULE_PERSISTENT) return SCD_ERR_ARG;
+  if (!p || schedule < SCD_SCHEDULE_AUTO || schedule > SCD_SCHEDULE_FUSED) return SCD_ERR_ARG;
   if (p->exact) return schedule == SCD_SCHEDULE_AUTO ? SCD_OK : SCD_ERR_UNSUPPORTED;
   int staged = 0;
   if (schedule == SCD_SCHEDULE_STAGES) {
     staged = 1;
+  } else if (schedule == SCD_SCHEDULE_FUSED) {
+    staged = 2;                                                 // falls back to 1 where it does not apply
   } else if (schedule == SCD_SCHEDULE_AUTO) {
     TuneEntry te;
-    staged = tune_lookup(batch_key(p), &te) ? te.schedule : default_staged(p->estimator);
+    staged = tune_lookup(batch_key(p), &te) ? te.schedule : default_staged(p->estimator, p->precision);
   }
   if (staged == p->staged) return SCD_OK;
   p->staged = staged;
@@ -762,6 +794,10 @@ scd_status scd_batch_tune(scd_batch_plan* p, const void* x_arena, const float* w
     }
   {                                                             // the staged schedule
     scd_status s = try_one(1, p->item_bytes, p->slot_bytes);
+    if (s != SCD_OK) return s;
+  }
+  if (p->estimator == 1 && p->precision == SCD_FP32) {          // ... with the fused SSCA kernels
+    scd_status s = try_one(2, p->item_bytes, p->slot_bytes);
     if (s != SCD_OK) return s;
   }
   p->staged = best_staged;
@@ -862,7 +898,8 @@ scd_status ssca_persistent(const float2* x, const float2* y, bool conj, int64_t 
 TuneEntry ssca_auto_choice(int64_t N, int Np, int precision) {
   TuneEntry e;
   if (tune_lookup(ssca_key(N, Np, precision), &e)) return e;
-  return TuneEntry{SCD_SCHEDULE_STAGES, kItemBytes, kSlotBytes, 0.0};
+  return TuneEntry{ssca_fused_supported(N, Np, precision) ? SCD_SCHEDULE_FUSED : SCD_SCHEDULE_STAGES, kItemBytes,
+                   kSlotBytes, 0.0};
 }
 
 void release_single_plans() {
@@ -887,6 +924,12 @@ extern "C" scd_status scd_ssca_tune(const void* x, int64_t N, int32_t Np, const 
   scd_status s = time_candidate(st, reps, [&]() { return scd_ssca(x, N, Np, window, out, &o); }, &ms);
   if (s != SCD_OK) return s;
   best.ms = ms;
+  if (ssca_fused_supported(N, Np, o.precision)) {
+    o.schedule = SCD_SCHEDULE_FUSED;
+    s = time_candidate(st, reps, [&]() { return scd_ssca(x, N, Np, window, out, &o); }, &ms);
+    if (s != SCD_OK) return s;
+    if (ms < best.ms) best = TuneEntry{SCD_SCHEDULE_FUSED, kItemBytes, kSlotBytes, ms};
+  }
   const int64_t items[] = {64ll << 10, 128ll << 10, 256ll << 10};
   const int64_t slots[] = {8ll << 20, 16ll << 20, 32ll << 20, 64ll << 20};
   for (int64_t item : items)

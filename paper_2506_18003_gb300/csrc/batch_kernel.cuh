@@ -279,9 +279,9 @@ cudaError_t launch_batch_profile(bool fam, bool tc, int grid, int smem, const Ba
 // the row pass / pair transforms reducing into alpha profiles.  Each launch runs a task list
 // whose tasks hold `first` and `subtiles` in CTA tiles; lists of kinds 1, 2, 4, 5 and 6 hold one
 // size class.
-cudaError_t staged_prepare(int kind, int M, bool tc, int* smem, int* per_sm);
-cudaError_t staged_launch(int kind, int M, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl, int nt,
-                          int64_t total, cudaStream_t st);
+cudaError_t staged_prepare(int kind, int M, int Np, bool tc, int* smem, int* per_sm);
+cudaError_t staged_launch(int kind, int M, int Np, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl,
+                          int nt, int64_t total, cudaStream_t st);
 
 }  // namespace bk
 }  // namespace scd

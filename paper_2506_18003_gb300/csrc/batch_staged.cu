@@ -12,6 +12,7 @@
 // [first_i, first_i + subtiles_i) and a CTA finds its task by binary search.  (A persistent
 // walk over the tiles kept more state live and spilled in the column pass.)
 #include "batch_kernel.cuh"
+#include "ssca_fused.cuh"
 
 namespace scd {
 namespace bk {
@@ -112,6 +113,43 @@ __global__ void __launch_bounds__(kThreads) k_st_rows(BatchArgs A, const Task* _
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
+// Fused SSCA (ssca_fused.cuh), one launch per size class N: tile A = channeliser + CDP + the
+// M1-point pass over m1 of column m2, clusters of Q CTAs (a task's tiles are m2 Q + q, and
+// every task's first tile is a multiple of Q, so a cluster never straddles two signals) ...
+template <int NP, int M1, int Q>
+__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kThreads, 2)
+    k_st_sfa(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  const int64_t tile = blockIdx.x;
+  const Task& t = tl[find_task(tl, nt, tile)];
+  const int local = (int)(tile - t.first);
+  ssca_chancol_tile<NP, M1, Q>(sm, A.x + t.x_off, A.y + t.x_off, A.conj != 0, t.N, t.M2, A.window, A.tw_np, t.tw,
+                               t.wN, A.ws + t.ws_off, local / Q, local % Q);
+}
+
+// ... and tile B = the M2-point pass over m2 for C consecutive q1 of one channel; PROF: each
+// bin reduced into the signal's alpha profile instead of stored.
+template <int M2, bool PROF>
+__global__ void __launch_bounds__(kThreads, M2 >= 1024 ? 2 : 3)
+    k_st_sfb(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
+  extern __shared__ __align__(128) float2 sm[];
+  constexpr int C = TileShape<M2>::C;
+  const int64_t tile = blockIdx.x;
+  const Task& t = tl[find_task(tl, nt, tile)];
+  const int64_t local = tile - t.first;
+  const int per = t.M1 / C;
+  const int64_t kh = local / per;
+  const int q10 = (int)(local % per) * C;
+  const float2* Yk = A.ws + t.ws_off + kh * t.N;
+  if constexpr (PROF) {
+    const int ah_off = (int)(kh - A.Np / 2) * (t.N / A.Np) + t.N / 2;
+    ssca_rowsf_tile<M2, true>(sm, Yk, nullptr, t.M1, t.tw, q10, reinterpret_cast<float*>(A.out) + t.out_off, ah_off,
+                              A.prof_power);
+  } else {
+    ssca_rowsf_tile<M2, false>(sm, Yk, A.out + t.out_off + kh * t.N, t.M1, t.tw, q10);
+  }
+}
+
 // FAM channelisers of all signals (X[kh][p] of signal i at ws + ws_off_i).
 template <int NP, bool TC>
 __global__ void __launch_bounds__(kThreads) k_st_fchan(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
@@ -172,6 +210,18 @@ cudaError_t prepare_t(K kernel, int smem, bool tc, int* smem_out, int* per_sm) {
   return e;
 }
 
+// Fused tile A of the size class N at Np channels (kind 7).
+template <int NP, int M1, int Q>
+cudaError_t prep_sfa(int* smem, int* per_sm) {
+  return prepare_t(k_st_sfa<NP, M1, Q>, ChanColSmem<NP, M1, Q>::total, false, smem, per_sm);
+}
+template <int NP, int M1, int Q>
+void launch_sfa(int grid, int smem, const BatchArgs& A, const Task* tl, int nt, int64_t total, cudaStream_t st) {
+  k_st_sfa<NP, M1, Q><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+}
+#define SCD_SFA_SHAPES(X) \
+  X(64, 64, 1) X(64, 128, 1) X(64, 256, 2) X(128, 64, 1) X(128, 128, 2) X(128, 256, 4) X(256, 64, 2) X(256, 128, 4)
+
 template <int M, bool TC>
 cudaError_t prep_m(int kind, int* smem, int* per_sm) {
   using S = TileShape<M>;
@@ -185,6 +235,10 @@ cudaError_t prep_m(int kind, int* smem, int* per_sm) {
   if constexpr (M <= 8192) {
     if (kind == 4) return prepare_t(k_st_fpairs<M, TC, false>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
     if (kind == 6) return prepare_t(k_st_fpairs<M, TC, true>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
+  }
+  if constexpr (M >= 64 && M <= 1024 && !TC) {
+    if (kind == 8) return prepare_t(k_st_sfb<M, false>, FftSmem<M, TileShape<M>::C, kThreads, false>::total, false, smem, per_sm);
+    if (kind == 9) return prepare_t(k_st_sfb<M, true>, FftSmem<M, TileShape<M>::C, kThreads, false>::total, false, smem, per_sm);
   }
   if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) return prepare_t(k_st_cols<M, TC>, ColsSmem<M, TC>::total, TC, smem, per_sm);
@@ -211,6 +265,10 @@ void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, 
     if (kind == 4) k_st_fpairs<M, TC, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
     if (kind == 6) k_st_fpairs<M, TC, true><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
   }
+  if constexpr (M >= 64 && M <= 1024 && !TC) {
+    if (kind == 8) k_st_sfb<M, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+    if (kind == 9) k_st_sfb<M, true><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  }
   if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) k_st_cols<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
     if (kind == 2) k_st_rows<M, TC, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
@@ -220,18 +278,31 @@ void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, 
 
 // kinds: SSCA 0 channeliser + CDP (M = Np in 16..256), 1 column pass (M = M1), 2 row pass
 // (M = M2), M1 and M2 in 64..1024; FAM 3 channeliser (M = Np), 4 pair transforms (M = P in
-// 2..8192); 5 and 6: kinds 2 and 4 reducing into alpha profiles
-bool valid(int kind, int M) {
+// 2..8192); 5 and 6: kinds 2 and 4 reducing into alpha profiles; fused SSCA (FP32 form):
+// 7 tile A (M = N, the split from fused_split(N, Np)), 8 tile B (M = M2 in 64..1024), 9 tile B
+// reducing into alpha profiles
+bool valid(int kind, int M, bool tc) {
   const bool pow2 = M >= 2 && (M & (M - 1)) == 0;
   if (kind == 0 || kind == 3) return pow2 && M >= 16 && M <= 256;
   if (kind == 4 || kind == 6) return pow2 && M <= 8192;
+  if (kind == 7) return !tc;
+  if (kind == 8 || kind == 9) return !tc && pow2 && M >= 64 && M <= 1024;
   return pow2 && M >= 64 && M <= 1024 && kind >= 1 && kind <= 5;
 }
 
 }  // namespace
 
-cudaError_t staged_prepare(int kind, int M, bool tc, int* smem, int* per_sm) {
-  if (!valid(kind, M)) return cudaErrorInvalidValue;
+cudaError_t staged_prepare(int kind, int M, int Np, bool tc, int* smem, int* per_sm) {
+  if (!valid(kind, M, tc)) return cudaErrorInvalidValue;
+  if (kind == 7) {
+    FusedSplit fs;
+    if (!fused_split(M, Np, &fs)) return cudaErrorInvalidValue;
+#define SCD_SFA_P(NPV, M1V, QV) \
+    if (Np == NPV && fs.M1 == M1V && fs.Q == QV) return prep_sfa<NPV, M1V, QV>(smem, per_sm);
+    SCD_SFA_SHAPES(SCD_SFA_P)
+#undef SCD_SFA_P
+    return cudaErrorInvalidValue;
+  }
 #define SCD_SP(MV) case MV: return tc ? prep_m<MV, true>(kind, smem, per_sm) : prep_m<MV, false>(kind, smem, per_sm);
   switch (M) {
     SCD_SP(2) SCD_SP(4) SCD_SP(8) SCD_SP(16) SCD_SP(32) SCD_SP(64) SCD_SP(128) SCD_SP(256) SCD_SP(512)
@@ -241,9 +312,21 @@ cudaError_t staged_prepare(int kind, int M, bool tc, int* smem, int* per_sm) {
 #undef SCD_SP
 }
 
-cudaError_t staged_launch(int kind, int M, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl, int nt,
-                          int64_t total, cudaStream_t st) {
-  if (!valid(kind, M)) return cudaErrorInvalidValue;
+cudaError_t staged_launch(int kind, int M, int Np, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl,
+                          int nt, int64_t total, cudaStream_t st) {
+  if (!valid(kind, M, tc)) return cudaErrorInvalidValue;
+  if (kind == 7) {
+    FusedSplit fs;
+    if (!fused_split(M, Np, &fs)) return cudaErrorInvalidValue;
+#define SCD_SFA_L(NPV, M1V, QV)                                                      \
+    if (Np == NPV && fs.M1 == M1V && fs.Q == QV) {                                   \
+      launch_sfa<NPV, M1V, QV>(grid, smem, A, tl, nt, total, st);                    \
+      return cudaGetLastError();                                                     \
+    }
+    SCD_SFA_SHAPES(SCD_SFA_L)
+#undef SCD_SFA_L
+    return cudaErrorInvalidValue;
+  }
 #define SCD_SL(MV) case MV: if (tc) launch_m<MV, true>(kind, grid, smem, A, tl, nt, total, st); else launch_m<MV, false>(kind, grid, smem, A, tl, nt, total, st); break;
   switch (M) {
     SCD_SL(2) SCD_SL(4) SCD_SL(8) SCD_SL(16) SCD_SL(32) SCD_SL(64) SCD_SL(128) SCD_SL(256) SCD_SL(512)

@@ -297,6 +297,45 @@ __device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2*
   }
 }
 
+// fft_batch with the pass-0 inputs already in registers: v[r] holds input t + r (M / r0) of
+// this thread's transform (the layout pass0_load gathers), for producers whose per-thread state
+// (coefficients held across several batches) does not fit the src(c, idx) form.  Same barriers
+// and dst contract as fft_batch; XSTRIDE > 0 sets the exchange stride of one transform (complex
+// values), otherwise PlanInfo<M>::stride(C).  With t-fast transforms of 8 threads (4 per warp)
+// the conflict-free stride is M + M / r0 (8 mod 16: the two transforms of a half-warp then fill
+// complementary banks in both the pass-0 stores and the pass-1 loads), where stride(C) costs two
+// wavefronts per access.
+template <int M, int C, bool CFAST, bool SYNC_DST, int XSTRIDE = 0, class Dst>
+__device__ __forceinline__ void fft_batch_from(float2* __restrict__ sm, const float2* __restrict__ tw,
+                                               float2 (&v)[PlanInfo<M>::E], Dst& dst) {
+  using PI = PlanInfo<M>;
+  using F = FftPieces<M>;
+  constexpr int T = PI::T;
+  const int tid = threadIdx.x;
+  const int c = CFAST ? (tid % C) : (tid / T);
+  const int t = CFAST ? (tid / C) : (tid % T);
+  float2* reg = sm + c * (XSTRIDE > 0 ? XSTRIDE : PI::stride(C));
+  dft<PI::r0>(v);
+  if constexpr (PI::n == 1) {
+    F::template pass_out<0>(c, t, dst, v);
+  } else {
+    F::pass0_store(t, reg, v);
+    team_sync<T, CFAST>();
+    F::template pass_load<1>(t, reg, tw, v);
+    if constexpr (PI::n == 2) {
+      if constexpr (SYNC_DST) __syncthreads();
+      F::template pass_out<1>(c, t, dst, v);
+    } else {
+      team_sync<T, CFAST>();
+      F::template pass_store<1>(t, reg, v);
+      team_sync<T, CFAST>();
+      F::template pass_load<2>(t, reg, tw, v);
+      if constexpr (SYNC_DST) __syncthreads();
+      F::template pass_out<2>(c, t, dst, v);
+    }
+  }
+}
+
 // Invokes F::template run<M>() for a runtime power-of-two M in [2, 16384].
 #define SCD_DISPATCH_POW2(M_RUNTIME, CALL)                     \
   switch (M_RUNTIME) {                                          \

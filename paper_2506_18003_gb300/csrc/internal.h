@@ -65,6 +65,14 @@ cudaError_t ssca_cols_tma(float2* ws, int64_t N, int Np, int M1, int M2, cudaStr
 // Stage 2: M2-point row FFTs, fftshifted into out[kh][sh]
 cudaError_t ssca_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st, int precision);
 
+// Fused schedule (ssca_fused.cu): tile A = channeliser + CDP + the M1-point pass over m1 and the
+// rotate factor, Y[kh][m2][q1] into ws; tile B = the M2-point pass over m2 into out[kh][sh].
+// Supported where fused_split (ssca_fused.cuh) fits the tiles, FP32 form.
+bool ssca_fused_supported(int64_t N, int Np, int precision);
+cudaError_t ssca_fused_chancol(const float2* x, const float2* y, bool conj, int64_t N, int Np, const float* window,
+                               float2* ws, cudaStream_t st);
+cudaError_t ssca_fused_rows(const float2* ws, int64_t N, int Np, float2* out, cudaStream_t st);
+
 // Default schedule of scd_ssca: one persistent launch (batch.cu) over a cached one-signal plan.
 size_t ssca_persistent_workspace(int64_t N, int Np);
 // y, conj: the channel-data product's second factor, as ssca_cdp
