@@ -170,9 +170,62 @@ def ssca_flops(Np, N):
     return N * (2 * Np + fft_flops(Np) + 12 * Np) + Np * fft_flops(N)
 
 
-def fp32_peak_tflops():
-    """FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz."""
-    return 152 * 128 * 2 * 2.07e9 / 1e12
+def fp32_peak_tflops(sm_count, clock_mhz):
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 FLOP (FMA) x SM clock."""
+    return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+def _oracle_worker_init():
+    # one thread per worker process: the pool supplies the parallelism
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_job(job):
+    """One signal of the batch through the FP64 oracle's full FAM and SSCA estimates, in a
+    worker process (the signal is regenerated from its seed); returns (samples consumed, s)."""
+    i, n, seed, fam_np, fam_l, P, ssca_np, N = job
+    from oracle import scd_oracle as orc
+    from paper_2506_18003_gb300 import signals
+    x = signals.batch_signal(i, n, seed=seed)
+    t0 = time.perf_counter()
+    orc.fam(x, orc.hamming_window(fam_np), fam_np, fam_l, P)
+    orc.ssca(x[:N].copy(), orc.hamming_window(ssca_np), ssca_np)
+    return (P - 1) * fam_l + fam_np + N, time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The FP64 oracle as it stands, one signal per task on every host core: a pool of spawned
+    worker processes (spawned, not forked, so that no worker inherits a CUDA context)."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init)
+        self.pool.map(_oracle_worker_init_probe, range(self.cores))      # workers up, imports done
+
+    def run(self, jobs):
+        """Wall time of the jobs spread over the pool; returns (samples consumed, seconds)."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_job, jobs, chunksize=1)
+        return sum(r[0] for r in res), time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _oracle_worker_init_probe(_):
+    from oracle import scd_oracle  # noqa: F401
+    from paper_2506_18003_gb300 import signals  # noqa: F401
+    return 0
 
 
 class BatchWorkload:
@@ -187,8 +240,8 @@ class BatchWorkload:
         self.tune = tune
         self.lengths = [int(v) for v in signals.batch_lengths(count)]
         # every rank processes its own independent signals (weak scaling)
-        self.sigs = [signals.batch_signal(i, n, seed=signals.seed_for(4, i + 1) + 7919 * rank)
-                     for i, n in enumerate(self.lengths)]
+        self.seeds = [signals.seed_for(4, i + 1) + 7919 * rank for i in range(len(self.lengths))]
+        self.sigs = [signals.batch_signal(i, n, seed=self.seeds[i]) for i, n in enumerate(self.lengths)]
         self.fam_P = [self._fam_P(n) for n in self.lengths]
         self.ssca_N = [self._ssca_N(n) for n in self.lengths]
 
@@ -220,6 +273,58 @@ class BatchWorkload:
 
     def samples_per_step(self):
         return self.fam_used() + sum(self.ssca_N)
+
+    def rates(self, stage_ms, ms_step):
+        """Per-estimator rates beside the headline (which sums both estimators' consumed
+        samples), and the rate at which the step consumes the input arena itself."""
+        fam_s, ssca_s = self.fam_used(), sum(self.ssca_N)
+        inp = int(sum(self.lengths))
+        return {"fam_msamples_per_s": round(fam_s / (stage_ms["fam_batch"] * 1e-3) / 1e6, 2),
+                "ssca_msamples_per_s": round(ssca_s / (stage_ms["ssca_batch"] * 1e-3) / 1e6, 2),
+                "input_msamples_per_s": round(inp / (ms_step * 1e-3) / 1e6, 2),
+                "fam_samples": fam_s, "ssca_samples": ssca_s, "input_samples": inp,
+                "value_is": "(FAM samples consumed + SSCA samples consumed) per step / step time: both "
+                            "estimators read the same input arena, each counted once"}
+
+    def oracle_jobs(self, idx):
+        return [(i, self.lengths[i], self.seeds[i], self.FAM_NP, self.FAM_L, self.fam_P[i], self.SSCA_NP,
+                 self.ssca_N[i]) for i in idx]
+
+    def cpu_baseline(self, pool):
+        """The FP64 oracle on every host core: one signal per worker, `cores` signals of the
+        batch at evenly spaced length quantiles, full FAM and SSCA estimates; the rate is the
+        sample's consumed samples over the wall time of the pool."""
+        import numpy as np
+        order = np.argsort(self.lengths)
+        k = pool.cores
+        pick = [int(order[len(order) * (j + 1) // (k + 1)]) for j in range(k)]
+        used, t = pool.run(self.oracle_jobs(pick))
+        desc = (f"{k} signals of the batch at evenly spaced length quantiles ({min(self.lengths[i] for i in pick)}"
+                f"..{max(self.lengths[i] for i in pick)} samples), full FAM and SSCA estimates, one signal per "
+                f"worker process ({k} processes, one thread each); rate = {used} samples consumed / {t:.2f} s wall")
+        return used / t / 1e6, t, desc
+
+    def reference_step(self, pool, k):
+        """Step k of the reference arm: `cores` signals shorter than 2^15 samples (a rotating
+        window over the batch), full FAM and SSCA estimates, one per worker."""
+        short = [i for i, n in enumerate(self.lengths) if n < (1 << 15)]
+        c = pool.cores
+        pick = [short[(k * c + j) % len(short)] for j in range(c)]
+        used, t = pool.run(self.oracle_jobs(pick))
+        desc = (f"per step {c} signals of the batch shorter than 2^15 samples (a rotating window), full FAM and "
+                f"SSCA estimates, one signal per worker process ({c} processes, one thread each)")
+        return used, t, desc
+
+    def parity_refs(self, nsig=3):
+        """Full FP64 oracle estimates of `nsig` signals (in this process, untimed) for the
+        parity check of both forms."""
+        import numpy as np
+        from oracle import scd_oracle as orc
+        order = np.argsort(self.lengths)
+        pick = [int(order[len(order) * (k + 1) // (nsig + 1)]) for k in range(nsig)]
+        af, as_ = orc.hamming_window(self.FAM_NP), orc.hamming_window(self.SSCA_NP)
+        self.oracle_refs = {i: (orc.fam(self.sigs[i], af, self.FAM_NP, self.FAM_L, self.fam_P[i]),
+                                orc.ssca(self.sigs[i][:self.ssca_N[i]], as_, self.SSCA_NP)) for i in pick}
 
     def points_per_step(self):
         return sum(self.FAM_NP ** 2 * P for P in self.fam_P) + sum(self.SSCA_NP * N for N in self.ssca_N)
@@ -322,11 +427,34 @@ class BatchWorkload:
                 ts += ev[1].elapsed_time(ev[2]) / reps
         binding.scd_check_device(stream)
         out_bytes = 4 * (plans[0][0].out_offsets[-1] + plans[1][0].out_offsets[-1])
+        # end to end in this output mode: input arena in from pinned host memory, both profile
+        # plans, both profile arenas out to pinned host memory, every step
+        xh = self.x.cpu().pin_memory()
+        hosts = [torch.empty(out.shape, dtype=out.dtype).pin_memory() for _, out in plans]
+
+        def one():
+            self.x.copy_(xh, non_blocking=True)
+            for pl, out in plans:
+                pl.run(self.x, out, self.ws, stream=stream)
+            for h, (_, out) in zip(hosts, plans):
+                h.copy_(out, non_blocking=True)
+            stream.synchronize()
+
+        with torch.cuda.stream(stream):
+            one()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                one()
+            dt = (time.perf_counter() - t0) / reps
         for pl, _ in plans:
             pl.close()
         return {"ms_per_step": round(tf + ts, 4), "stage_ms": {"fam_batch": round(tf, 4), "ssca_batch": round(ts, 4)},
                 "msamples_per_s": round(self.samples_per_step() / ((tf + ts) * 1e-3) / 1e6, 2),
                 "output_bytes_per_step": out_bytes,
+                "e2e": {"value": round(self.samples_per_step() / dt / 1e6, 2), "unit": "Msamples/s",
+                        "ms_per_step": round(dt * 1e3, 3), "h2d_bytes_per_step": xh.numel() * 8,
+                        "d2h_bytes_per_step": out_bytes,
+                        "api": "BatchPlan.run in alpha-profile mode with torch pinned-host copies in and out"},
                 "note": "alpha profiles (|S| max over f per alpha) fused into the last stage; FP32 form; tuned"}
 
     def exact_ssca(self, torch, binding, stream, reps=3):
@@ -378,35 +506,6 @@ class BatchWorkload:
         return {"value": world * self.samples_per_step() * steps / dt / 1e6, "unit": "Msamples/s",
                 "h2d_bytes_per_step": xh.numel() * 8, "d2h_bytes_per_step": (of.numel() + os_.numel()) * 8,
                 "steps": steps, "api": "BatchPlan.run (scd_batch_run) with torch pinned-host copies in and out"}
-
-    def oracle_sample(self, nsig=3, reduced=False):
-        """FP64 oracle on `nsig` signals of the batch (FAM and SSCA each), extrapolated by
-        samples consumed to the whole step."""
-        import numpy as np
-        from oracle import scd_oracle as orc
-        order = np.argsort(self.lengths)
-        pick = [int(order[len(order) * (k + 1) // (nsig + 1)]) for k in range(nsig)]
-        af, as_ = orc.hamming_window(self.FAM_NP), orc.hamming_window(self.SSCA_NP)
-        self.oracle_refs = {}
-        used = 0
-        t0 = time.perf_counter()
-        for i in pick:
-            P, N = self.fam_P[i], self.ssca_N[i]
-            if reduced:                       # reference arm: a quarter of the pairs and channels
-                sel = np.arange(0, self.FAM_NP ** 2, 4)
-                orc.fam_pairs(self.sigs[i], af, self.FAM_NP, self.FAM_L, P, sel // self.FAM_NP, sel % self.FAM_NP)
-                used += ((P - 1) * self.FAM_L + self.FAM_NP) // 4
-                orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP, channels=np.arange(0, self.SSCA_NP, 4))
-                used += N // 4
-            else:
-                self.oracle_refs[i] = (orc.fam(self.sigs[i], af, self.FAM_NP, self.FAM_L, P),
-                                       orc.ssca(self.sigs[i][:N], as_, self.SSCA_NP))
-                used += (P - 1) * self.FAM_L + self.FAM_NP + N
-        t = time.perf_counter() - t0
-        what = "a quarter of the FAM pairs and SSCA channels" if reduced else "full FAM and SSCA estimates"
-        desc = (f"{nsig} signals of the batch (lengths {[self.lengths[i] for i in pick]}), {what}; time "
-                f"scaled by samples consumed ({used} of {self.samples_per_step()} per step)")
-        return t * self.samples_per_step() / used, desc
 
 
 class PaperScaleWorkload:
@@ -575,19 +674,38 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = WORKLOADS[args.workload]()
-    steps, desc = [], ""
-    for i in range(args.warmup + args.steps):
-        t, desc = wl.oracle_sample(reduced=True)
-        if i >= args.warmup:
-            steps.append(t)
-    t = statistics.mean(steps)
-    v = wl.samples_per_step() / t / 1e6
+    if hasattr(wl, "reference_step"):
+        # the FP64 oracle on every host core, each step a real (not extrapolated) sample of the
+        # workload: value = the samples those steps consumed / the time they took
+        pool = OraclePool()
+        used = secs = 0.0
+        desc = ""
+        for k in range(args.warmup + args.steps):
+            u, t, desc = wl.reference_step(pool, k)
+            if k >= args.warmup:
+                used += u
+                secs += t
+        pool.close()
+        cores = pool.cores
+        v = used / secs / 1e6
+        ms = secs / args.steps * 1e3
+    else:
+        steps = []
+        desc = ""
+        for i in range(args.warmup + args.steps):
+            t, desc = wl.oracle_sample(reduced=True)
+            if i >= args.warmup:
+                steps.append(t)
+        t = statistics.mean(steps)
+        cores = 1
+        v = wl.samples_per_step() / t / 1e6
+        ms = t * 1e3
+        desc += "; numpy FFT and elementwise kernels on one thread"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Msamples/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": wl.desc(),
-            "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: " + desc + "; numpy FFT and elementwise kernels on one thread"},
+            "cpu_baseline": {"value": v, "unit": "Msamples/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -789,6 +907,9 @@ def run_ours(args):
     world, rank, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
+    oracle_pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "batch":
+        oracle_pool = OraclePool()          # worker processes spawned before this process touches the GPU
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -853,19 +974,24 @@ def run_ours(args):
     # roofline of the dominant kernel: whichever floor is higher, its algorithmic bytes at the
     # measured HBM bandwidth or its algorithmic FLOPs at the FP32 CUDA-core peak
     kf = wl.kernel_flops()
-    alu_peak = fp32_peak_tflops()
+    # FP32 CUDA-core peak from this device's SM count and the SM clock sampled under load
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    alu_peak = fp32_peak_tflops(sm_count, clock_mhz)
     alu_bound = kf[top] / (alu_peak * 1e12) > kb[top] / (hbm * 1e9)
     ach_gbs = kb[top] / (stage_ms[top] * 1e-3) / 1e9
     ach_tf = kf[top] / (stage_ms[top] * 1e-3) / 1e12
     if alu_bound:
         roof = {"bound": "alu", "kernel": top, "achieved": ach_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ach_tf / alu_peak, "peak_source": "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x "
-                "2 FLOP x 2.07 GHz", "algorithmic_flops": kf[top], "hbm_frac": ach_gbs / hbm,
-                "algorithmic_bytes": kb[top]}
+                "frac": ach_tf / alu_peak, "peak_source": f"derived FP32 CUDA-core peak: sm_count x 128 lanes x "
+                f"2 FLOP x clock_mhz (median SM clock sampled in the timed region)", "sm_count": sm_count,
+                "clock_mhz": clock_mhz, "algorithmic_flops": kf[top], "hbm_frac": ach_gbs / hbm,
+                "hbm_peak": hbm, "algorithmic_bytes": kb[top]}
     else:
         roof = {"bound": "hbm", "kernel": top, "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": ach_gbs / hbm, "peak_source": peak_src, "algorithmic_bytes": kb[top],
-                "alu_frac": ach_tf / alu_peak, "algorithmic_flops": kf[top]}
+                "alu_frac": ach_tf / alu_peak, "alu_peak": alu_peak, "sm_count": sm_count, "clock_mhz": clock_mhz,
+                "algorithmic_flops": kf[top]}
     roof["traffic"] = captured_traffic(top) if prec == "fp32" else None
     if roof["traffic"]:
         # the captured DRAM bytes at the live stage time, against the copy bandwidth: how close
@@ -881,6 +1007,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "stage_ms": {k: round(v, 5) for k, v in stage_ms.items()},
         "roofline": roof,
+        "rates": wl.rates(stage_ms, ms_step) if hasattr(wl, "rates") else None,
         "stage_hbm_frac": {k: round(kb[k] / (v * 1e-3) / 1e9 / hbm, 4) for k, v in stage_ms.items() if v > 0},
         "stage_alu_frac": {k: round(kf[k] / (v * 1e-3) / 1e12 / alu_peak, 4) for k, v in stage_ms.items()
                            if v > 0 and kf[k]},
@@ -902,9 +1029,16 @@ def run_ours(args):
             line["ssca_exact_lengths"] = wl.exact_ssca(torch, binding, stream)
         line["variants"] = measure_variants(torch, binding, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, desc = wl.oracle_sample()
-        line["cpu_baseline"] = {"value": wl.samples_per_step() / t / 1e6, "unit": "Msamples/s", "cores": 1,
-                                "kind": "oracle", "sample": desc + "; numpy FFT and elementwise kernels on one thread"}
+        if hasattr(wl, "cpu_baseline"):
+            v, t, desc = wl.cpu_baseline(oracle_pool)
+            line["cpu_baseline"] = {"value": v, "unit": "Msamples/s", "cores": oracle_pool.cores, "kind": "oracle",
+                                    "sample": desc, "wall_s": round(t, 3)}
+            oracle_pool.close()
+            wl.parity_refs()
+        else:
+            t, desc = wl.oracle_sample()
+            line["cpu_baseline"] = {"value": wl.samples_per_step() / t / 1e6, "unit": "Msamples/s", "cores": 1,
+                                    "kind": "oracle", "sample": desc + "; numpy FFT and elementwise kernels on one thread"}
         if getattr(wl, "oracle_refs", None):
             with torch.cuda.stream(stream):
                 line["cpu_baseline"]["parity"] = wl.parity_sample(stream)

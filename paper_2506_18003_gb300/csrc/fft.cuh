@@ -190,8 +190,9 @@ struct FftPieces {
 #pragma unroll
     for (int j = 0; j < R; ++j) reg[PI::pad(t * R + j)] = v[j];
   }
-  // pass S >= 1: load from shared memory with twiddles and run the DFTs
-  template <int S>
+  // pass S >= 1: load from shared memory with twiddles and run the DFTs (TWS: the twiddle
+  // table is a copy in shared memory, read with plain loads instead of the read-only path)
+  template <int S, bool TWS = false>
   __host__ __device__ __forceinline__ static void pass_load(int t, const float2* reg, const float2* tw, float2* v) {
     constexpr int R = PI::R(S), p = PI::p(S), B = E / R;
 #pragma unroll
@@ -201,7 +202,7 @@ struct FftPieces {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         float2 x = reg[PI::pad(i + r * (M / R))];
-        if (r > 0) x = cmul(x, SCD_LDG(tw + PI::off(S) + r * p + k));
+        if (r > 0) x = cmul(x, TWS ? tw[PI::off(S) + r * p + k] : SCD_LDG(tw + PI::off(S) + r * p + k));
         v[b * R + r] = x;
       }
       dft<R>(v + b * R);
@@ -305,7 +306,7 @@ __device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2*
 // the conflict-free stride is M + M / r0 (8 mod 16: the two transforms of a half-warp then fill
 // complementary banks in both the pass-0 stores and the pass-1 loads), where stride(C) costs two
 // wavefronts per access.
-template <int M, int C, bool CFAST, bool SYNC_DST, int XSTRIDE = 0, class Dst>
+template <int M, int C, bool CFAST, bool SYNC_DST, int XSTRIDE = 0, bool TWS = false, class Dst>
 __device__ __forceinline__ void fft_batch_from(float2* __restrict__ sm, const float2* __restrict__ tw,
                                                float2 (&v)[PlanInfo<M>::E], Dst& dst) {
   using PI = PlanInfo<M>;
@@ -321,7 +322,7 @@ __device__ __forceinline__ void fft_batch_from(float2* __restrict__ sm, const fl
   } else {
     F::pass0_store(t, reg, v);
     team_sync<T, CFAST>();
-    F::template pass_load<1>(t, reg, tw, v);
+    F::template pass_load<1, TWS>(t, reg, tw, v);
     if constexpr (PI::n == 2) {
       if constexpr (SYNC_DST) __syncthreads();
       F::template pass_out<1>(c, t, dst, v);
@@ -329,7 +330,7 @@ __device__ __forceinline__ void fft_batch_from(float2* __restrict__ sm, const fl
       team_sync<T, CFAST>();
       F::template pass_store<1>(t, reg, v);
       team_sync<T, CFAST>();
-      F::template pass_load<2>(t, reg, tw, v);
+      F::template pass_load<2, TWS>(t, reg, tw, v);
       if constexpr (SYNC_DST) __syncthreads();
       F::template pass_out<2>(c, t, dst, v);
     }

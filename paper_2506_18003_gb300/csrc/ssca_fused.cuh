@@ -80,7 +80,11 @@ struct ChanColSmem {
   static constexpr int SX = M1 + 8;
   static constexpr int xs_off = exch;
   static constexpr int rot_off = xs_off + up128(G * SX * 8);
-  static constexpr int total = rot_off + M1 * 8;
+  // the tile's rotated window, and the pass twiddles of both transform sizes, staged once
+  static constexpr int win_off = rot_off + up128(M1 * 8);
+  static constexpr int twn_off = win_off + up128(NP * 4);
+  static constexpr int twm_off = twn_off + up128(PlanInfo<NP>::tw_len() * 8);
+  static constexpr int total = twm_off + up128(PlanInfo<M1>::tw_len() * 8);
 };
 
 // Position of X_g(m1, channel kappa) in a CTA's block.  The swizzle depends on how many threads
@@ -122,39 +126,50 @@ __device__ __forceinline__ void ssca_chancol_tile(float2* sm, const float2* __re
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   float2* xs = reinterpret_cast<float2*>(base + Lay::xs_off);
   float2* rot = reinterpret_cast<float2*>(base + Lay::rot_off);
+  float* win = reinterpret_cast<float*>(base + Lay::win_off);
+  float2* twn = reinterpret_cast<float2*>(base + Lay::twn_off);
+  float2* twm = reinterpret_cast<float2*>(base + Lay::twm_off);
   const int tid = threadIdx.x;
   const int CY = rowsf_c(M2);                           // Y's column blocks (yf_index)
   const int lcy = CY == 8 ? 3 : (CY == 16 ? 4 : 5);
+  const int smod = (m2 - NP / 2) & (NP - 1);            // s mod Np for every m1 (Np divides M2)
   if constexpr (Q > 1) cluster_arrive_relaxed();        // every CTA of the cluster has started ...
   for (int i = tid; i < M1; i += 256) rot[i] = __ldg(wN + (((int64_t)i * m2) & (N - 1)));   // W_N^{q1 m2}
+  for (int j = tid; j < NP; j += 256) win[j] = __ldg(a + ((j - smod) & (NP - 1)));         // a[rho] at input j
+  for (int i = tid; i < PlanInfo<NP>::tw_len(); i += 256) twn[i] = __ldg(tw_np + i);
+  for (int i = tid; i < PlanInfo<M1>::tw_len(); i += 256) twm[i] = __ldg(tw_m1 + i);
+  __syncthreads();
 
-  // ---- channeliser + CDP: batches of CA time points (transforms t-fast: c = tid / TG)
+  // ---- channeliser + CDP: batches of CA time points (transforms t-fast: c = tid / TG); the
+  // samples of the next batch are loaded while this batch is transformed
   {
     const int c = tid / TG, t = tid % TG;
-    const int smod = (m2 - NP / 2) & (NP - 1);          // s mod Np for every m1 (Np divides M2)
-    float wa[EG];                                       // window of FFT input j = t + i TG ...
-    int off[EG];                                        // ... and its sample offset rho - Np/2 from n
-#pragma unroll
-    for (int i = 0; i < EG; ++i) {
-      const int rho = (t + i * TG - smod) & (NP - 1);
-      wa[i] = __ldg(a + rho);
-      off[i] = rho - NP / 2;
-    }
-    if constexpr (Q > 1) cluster_wait_acquire();       // ... before any store into a peer's block
-    for (int bt = 0; bt < MQ / CA; ++bt) {
+    constexpr int NB = MQ / CA;
+    // FFT input j = t + i TG takes the sample rho - Np/2 after n, rho = (j - smod) mod Np
+    auto load = [&](int bt, float2 (&xv)[EG]) {
       const int m1 = q * MQ + bt * CA + c;
       const int n = m1 * M2 + m2;
-      float2 v[EG];
       // only the first and the last time point of a column have window samples outside [0, N)
       const bool edge = m1 == 0 || m1 == M1 - 1;
 #pragma unroll
       for (int i = 0; i < EG; ++i) {
-        const int idx = n + off[i];
-        const float2 xv =
-            (!edge || (idx >= 0 && idx < N)) ? __ldg(x + (edge ? max(0, min(idx, N - 1)) : idx)) : make_float2(0.f, 0.f);
-        v[i] = cscale(xv, wa[i]);
+        const int idx = n + ((t + i * TG - smod) & (NP - 1)) - NP / 2;
+        xv[i] = (!edge || (idx >= 0 && idx < N)) ? __ldg(x + (edge ? max(0, min(idx, N - 1)) : idx))
+                                                 : make_float2(0.f, 0.f);
       }
+    };
+    float2 xnext[EG];
+    load(0, xnext);
+    if constexpr (Q > 1) cluster_wait_acquire();       // ... before any store into a peer's block
+#pragma unroll 1
+    for (int bt = 0; bt < NB; ++bt) {
+      const int m1 = q * MQ + bt * CA + c;
+      const int n = m1 * M2 + m2;
+      float2 v[EG];
+#pragma unroll
+      for (int i = 0; i < EG; ++i) v[i] = cscale(xnext[i], win[t + i * TG]);
       float2 yn = __ldg(y + n);                         // the factor is conj(yn)
+      if (bt + 1 < NB) load(bt + 1, xnext);
       if (conj) yn.y = -yn.y;
       auto dst = [&](int, int f, float2 val) {
         const int kh = (f + NP / 2) & (NP - 1);
@@ -162,7 +177,7 @@ __device__ __forceinline__ void ssca_chancol_tile(float2* sm, const float2* __re
         if constexpr (Q > 1) p = cooperative_groups::this_cluster().map_shared_rank(p, (unsigned)(kh / G));
         *p = cmulc(val, yn);
       };
-      fft_batch_from<NP, CA, false, false, tfast_stride<NP>()>(sm, tw_np, v, dst);
+      fft_batch_from<NP, CA, false, false, tfast_stride<NP>(), true>(sm, twn, v, dst);
       __syncwarp();                                     // this warp's exchange reads precede the next batch's writes
     }
   }
@@ -184,7 +199,7 @@ __device__ __forceinline__ void ssca_chancol_tile(float2* sm, const float2* __re
 #pragma unroll
       for (int i = 0; i < PM::E; ++i) v[i] = xs[xs_pos<TG>(kappa, t + i * TM, Lay::SX)];
       auto dst = [&](int, int q1, float2 val) { yo[(int64_t)(q1 >> lcy) * M2 * CY + (q1 & (CY - 1))] = cmul(val, rot[q1]); };
-      fft_batch_from<M1, CB, false, false, tfast_stride<M1>()>(sm, tw_m1, v, dst);
+      fft_batch_from<M1, CB, false, false, tfast_stride<M1>(), true>(sm, twm, v, dst);
       __syncwarp();
     }
   }

@@ -3,7 +3,7 @@
     python -m paper_2506_18003_gb300.profile_case ssca --N 262144 --Np 256 --reps 3
     python -m paper_2506_18003_gb300.profile_case fam --N 65728 --Np 256 --L 64 --P 1024 --reps 3
     python -m paper_2506_18003_gb300.profile_case batch_fam --N 0 --Np 64 --L 16 --nsig 64 --reps 2
-    python -m paper_2506_18003_gb300.profile_case batch_ssca --N 0 --Np 128 --nsig 32 --schedule stages
+    python -m paper_2506_18003_gb300.profile_case batch_ssca --N 0 --Np 128 --nsig 32 --schedule fused
 
 Inputs are seeded white noise (the kernels' cost does not depend on the values).  Prints
 the CUDA-event time of each call.
@@ -31,7 +31,7 @@ def main() -> int:
     ap.add_argument("--P", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--schedule", default="auto", help="batch_ssca: auto, stages or persistent")
+    ap.add_argument("--schedule", default="auto", help="ssca, batch_ssca: auto, stages, persistent or fused")
     a = ap.parse_args()
 
     if a.estimator.startswith("batch_"):
@@ -67,7 +67,7 @@ def main() -> int:
         if a.estimator == "fam":
             binding.scd_fam(x, a.Np, a.L, a.P, out=out, precision=a.precision)
         elif a.estimator == "ssca":
-            binding.scd_ssca(x, a.Np, out=out, precision=a.precision)
+            binding.scd_ssca(x, a.Np, out=out, precision=a.precision, schedule=a.schedule)
         elif a.estimator == "fam_map":
             binding.scd_fam_map(out, a.Np, a.L, a.P, map=mp)
         else:

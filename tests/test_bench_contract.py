@@ -36,4 +36,5 @@ def test_flop_model_hand_counts():
     # SSCA at Np=256, N=2^20: per point 2 + 5*8 + 12 per channel, per channel 5 N log2 N
     N = 1 << 20
     assert bench.ssca_flops(256, N) == N * (512 + 10240 + 3072) + 256 * 5 * N * 20
-    assert abs(bench.fp32_peak_tflops() - 80.54784) < 1e-9
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.54784) < 1e-9     # 152 SMs at 2.07 GHz
+    assert abs(bench.fp32_peak_tflops(148, 1965.0) - 148 * 128 * 2 * 1.965e-3) < 1e-9
