@@ -459,7 +459,8 @@ class BatchWorkload:
 
     def exact_ssca(self, torch, binding, stream, reps=3):
         """The batch's SSCA without truncation (exact-length plan: N_i = len_i, Bluestein for
-        the lengths that are not powers of two, one signal after the other), FP32, outside the
+        the lengths that are not powers of two; one CUDA graph: the input preparation and the
+        channeliser over every signal, then three passes per cyclic length), FP32, outside the
         step: CUDA events around `reps` runs after one warm-up."""
         plan = binding.BatchPlan("ssca", self.lengths, self.SSCA_NP, 1, "fp32", exact=True)
         out = torch.empty(plan.out_offsets[-1], dtype=torch.complex64, device=self.x.device)
@@ -476,8 +477,9 @@ class BatchWorkload:
         ms = t0.elapsed_time(t1) / reps
         used = int(sum(self.lengths))
         res = {"ms": round(ms, 3), "samples": used, "msamples_per_s": round(used / (ms * 1e-3) / 1e6, 2),
-               "note": "every sample of the 512 signals (the step's SSCA uses the largest "
-                                             "power of two of each length); FP32"}
+               "workspace_bytes": int(plan.workspace_bytes),
+               "note": "every sample of the 512 signals (the step's SSCA uses the largest power of two of each "
+                       "length); Bluestein's identity with cyclic lengths up to 2^19; FP32; one graph per run"}
         plan.close()
         del out, ws
         torch.cuda.empty_cache()

@@ -74,7 +74,7 @@ int tile_c(int M) {                       // transforms per tile for size M (256
     case 128: return TileShape<128>::C;   case 256: return TileShape<256>::C;
     case 512: return TileShape<512>::C;   case 1024: return TileShape<1024>::C;
     case 2048: return TileShape<2048>::C; case 4096: return TileShape<4096>::C;
-    case 8192: return TileShape<8192>::C;
+    case 8192: return TileShape<8192>::C; case 16384: return TileShape<16384>::C;
     default: return 0;
   }
 }
@@ -504,6 +504,172 @@ scd_status plan_create(int32_t estimator, int32_t nsig, const int64_t* lengths, 
   *out = p;
   return SCD_OK;
 }
+// Task lists and launches of an exact-length plan (batch_exact.cu describes the stages).
+scd_status build_exact(scd_batch_plan* p) {
+  using namespace scd;
+  const int nsig = p->nsig, Np = p->Np;
+  const bool fam = p->estimator == 0, tc = p->precision == SCD_SPLIT_BF16;
+  cudaError_t e;
+  p->st_tasks.clear();
+  p->st_launches.clear();
+  auto launch_of = [&](int kind, int M, int first_task) -> scd_status {
+    scd_batch_plan::StageLaunch L{kind, M, first_task, (int)p->st_tasks.size() - first_task, 0, 0, 0};
+    if (L.count == 0) return SCD_OK;
+    int64_t tiles = 0;
+    for (int i = first_task; i < (int)p->st_tasks.size(); ++i) {
+      p->st_tasks[i].first = tiles;
+      tiles += p->st_tasks[i].subtiles;
+    }
+    L.total = tiles;
+    int per_sm = 0;
+    cudaError_t ee = staged_prepare(kind, M, Np, tc, &L.smem, &per_sm);
+    if (ee != cudaSuccess) return cuda_status(ee);
+    if (tiles < 1) return SCD_ERR_INTERNAL;
+    if (tiles >= (int64_t)0x7FFFFFFF) return SCD_ERR_UNSUPPORTED;
+    L.grid = (int)tiles;
+    p->st_launches.push_back(L);
+    return SCD_OK;
+  };
+  auto base_task = [&](int i) {
+    Task t{};
+    t.dep = -1;
+    t.dep2 = -1;
+    t.x_off = p->x_off[i];
+    t.out_off = p->out_off[i];
+    return t;
+  };
+  const int cnp = tile_c(Np);
+  int64_t off = 0;                                              // workspace elements
+  auto take = [&](int64_t n) { const int64_t o = off; off += (n + 31) / 32 * 32; return o; };
+  std::vector<int64_t> ws(nsig), xp(nsig), padded(nsig), cyc(nsig);
+  scd_status ls;
+  if (fam) {
+    // channelisers of every signal (X_i: Np x P_i), then per size class the pair transforms
+    int f0 = 0;
+    for (int i = 0; i < nsig; ++i) {
+      Task t = base_task(i);
+      t.P = (int)p->sizes[i];
+      t.ws_off = ws[i] = take((int64_t)Np * t.P);
+      t.subtiles = (t.P + cnp - 1) / cnp;
+      p->st_tasks.push_back(t);
+    }
+    if ((ls = launch_of(3, Np, f0)) != SCD_OK) return ls;
+    std::vector<int64_t> classes;
+    for (int i = 0; i < nsig; ++i) classes.push_back(is_pow2(p->sizes[i]) ? p->sizes[i] : -bluestein_len_host(p->sizes[i]));
+    std::sort(classes.begin(), classes.end());
+    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+    for (int64_t cls : classes) {                                 // > 0: power of two P; < 0: cyclic length
+      const int M = (int)(cls > 0 ? cls : -cls);
+      f0 = (int)p->st_tasks.size();
+      for (int i = 0; i < nsig; ++i) {
+        const int64_t P = p->sizes[i];
+        const bool mine = cls > 0 ? P == cls : (!is_pow2(P) && bluestein_len_host(P) == M);
+        if (!mine) continue;
+        Task t = base_task(i);
+        t.P = (int)P;
+        t.size = M;
+        t.ws_off = ws[i];
+        t.subtiles = ((int64_t)Np * Np + tile_c(M) - 1) / tile_c(M);
+        if (!(t.tw = table_pass(M, &e))) return cuda_status(e);
+        if (cls < 0 && (!(t.chirp = table_chirp(P, &e)) || !(t.bh = table_bluestein(P, M, &e)))) return cuda_status(e);
+        if (tc && !(t.bmats = table_tc_bmats(M, &t.bbytes, &e))) return cuda_status(e);
+        p->st_tasks.push_back(t);
+      }
+      if ((ls = launch_of(cls > 0 ? 4 : 14, M, f0)) != SCD_OK) return ls;
+    }
+  } else {
+    for (int i = 0; i < nsig; ++i) {
+      const int64_t N = p->sizes[i];
+      if (is_pow2(N)) {
+        padded[i] = N;
+        cyc[i] = N;
+        xp[i] = -1;
+        ws[i] = take((int64_t)Np * N);
+      } else {
+        padded[i] = (N + cnp - 1) / cnp * cnp;
+        cyc[i] = bluestein_len_host(N);
+        xp[i] = take(2 * padded[i]);                            // xp then yp, padded[i] apart
+        ws[i] = take((int64_t)Np * cyc[i]);
+      }
+    }
+    // kind 10: padded inputs with the chirp folded into the second factor
+    int f0 = (int)p->st_tasks.size();
+    for (int i = 0; i < nsig; ++i) {
+      if (xp[i] < 0) continue;
+      Task t = base_task(i);
+      t.N = (int)p->sizes[i];
+      t.P = (int)padded[i];
+      t.xp_off = xp[i];
+      t.yp_off = xp[i] + padded[i];
+      t.subtiles = (padded[i] + exact_prep_per_tile() - 1) / exact_prep_per_tile();
+      if (!(t.chirp = table_chirp(t.N, &e))) return cuda_status(e);
+      p->st_tasks.push_back(t);
+    }
+    if ((ls = launch_of(10, 0, f0)) != SCD_OK) return ls;
+    // kind 0: every signal's channeliser + CDP (rows of the cyclic length for Bluestein signals)
+    f0 = (int)p->st_tasks.size();
+    for (int i = 0; i < nsig; ++i) {
+      Task t = base_task(i);
+      t.N = (int)padded[i];
+      t.ws_off = ws[i];
+      if (xp[i] >= 0) {
+        t.in_ws = 1;
+        t.xp_off = xp[i];
+        t.yp_off = xp[i] + padded[i];
+        t.ld = cyc[i];
+      }
+      t.subtiles = padded[i] / cnp;
+      p->st_tasks.push_back(t);
+    }
+    if ((ls = launch_of(0, Np, f0)) != SCD_OK) return ls;
+    // per transform size: the staged column and row passes (powers of two) or the three
+    // Bluestein passes (cyclic lengths)
+    std::vector<int64_t> classes;
+    for (int i = 0; i < nsig; ++i) classes.push_back(xp[i] < 0 ? p->sizes[i] : -cyc[i]);
+    std::sort(classes.begin(), classes.end());
+    classes.erase(std::unique(classes.begin(), classes.end()), classes.end());
+    for (int64_t cls : classes) {
+      const int64_t M = cls > 0 ? cls : -cls;
+      int M1, M2;
+      ssca_split(M, &M1, &M2);
+      const int kinds_pow2[] = {1, 2}, kinds_bl[] = {11, 12, 13};
+      const int* kinds = cls > 0 ? kinds_pow2 : kinds_bl;
+      const int nk = cls > 0 ? 2 : 3;
+      for (int ki = 0; ki < nk; ++ki) {
+        const int kind = kinds[ki];
+        const int size = (kind == 2 || kind == 12) ? M2 : M1;
+        f0 = (int)p->st_tasks.size();
+        for (int i = 0; i < nsig; ++i) {
+          const bool mine = cls > 0 ? (xp[i] < 0 && p->sizes[i] == cls) : (xp[i] >= 0 && cyc[i] == M);
+          if (!mine) continue;
+          Task t = base_task(i);
+          t.N = (int)p->sizes[i];
+          t.P = (int)padded[i];
+          t.M1 = M1; t.M2 = M2; t.size = size;
+          t.ws_off = ws[i];
+          t.subtiles = (kind == 2 || kind == 12) ? (int64_t)Np * (M1 / tile_c(M2)) : (int64_t)Np * (M2 / tile_c(M1));
+          if (!(t.tw = table_pass(size, &e))) return cuda_status(e);
+          if ((kind == 1 || kind == 11 || kind == 13) &&
+              (!(t.wN = table_roots((int)M, &e)) || !(t.cols = table_cols((int)M, M1, tile_c(M1), &e))))
+            return cuda_status(e);
+          if (kind == 12 && !(t.bh = table_bluestein_rows(t.N, M, M1, &e))) return cuda_status(e);
+          if (kind == 13 && !(t.chirp = table_chirp(t.N, &e))) return cuda_status(e);
+          if (tc && !(t.bmats = table_tc_bmats(size, &t.bbytes, &e))) return cuda_status(e);
+          p->st_tasks.push_back(t);
+        }
+        if ((ls = launch_of(kind, size, f0)) != SCD_OK) return ls;
+      }
+    }
+  }
+  p->ws_bytes = sizeof(float2) * (size_t)off;
+  if ((e = cudaMalloc(&p->d_st, sizeof(Task) * p->st_tasks.size())) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_st, p->st_tasks.data(), sizeof(Task) * p->st_tasks.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMalloc(&p->d_counters, sizeof(unsigned))) != cudaSuccess) return cuda_status(e);
+  return SCD_OK;
+}
+
 // Exact-length plan: every signal's estimate at the sizes its length gives (FAM P_i =
 // floor((len_i - Np)/L) + 1, SSCA N_i = len_i), run with the single-estimate kernels (Bluestein's
 // identity for the sizes that are not powers of two) one signal after the other on the stream.
@@ -523,7 +689,6 @@ scd_status plan_create_exact(int32_t estimator, int32_t nsig, const int64_t* len
   if (e != cudaSuccess) { free_plan(p); return cuda_status(e); }
   p->x_off.assign(nsig + 1, 0); p->out_off.assign(nsig + 1, 0); p->ws_off.assign(nsig + 1, 0);
   p->sizes.assign(nsig, 0); p->used.assign(nsig, 0);
-  size_t ws = 0;
   for (int i = 0; i < nsig; ++i) {
     const int64_t len = lengths[i];
     if (len < 1) { free_plan(p); return SCD_ERR_ARG; }
@@ -533,13 +698,11 @@ scd_status plan_create_exact(int32_t estimator, int32_t nsig, const int64_t* len
       sz = (len - Np) / L + 1;
       if (sz > 16384 || (!is_pow2(sz) && sz > 8192)) { free_plan(p); return SCD_ERR_UNSUPPORTED; }
       p->used[i] = (sz - 1) * L + Np;
-      ws = std::max(ws, scd_fam_workspace_bytes(p->used[i], Np, L, (int32_t)sz, precision));
     } else {
       sz = len;
       if (sz < 4096) { free_plan(p); return SCD_ERR_ARG; }
       if (sz > (1 << 20) || (!is_pow2(sz) && sz > (1 << 19))) { free_plan(p); return SCD_ERR_UNSUPPORTED; }
       p->used[i] = sz;
-      ws = std::max(ws, is_pow2(sz) ? sizeof(float2) * (size_t)Np * sz : ssca_any_workspace(sz, Np));
     }
     p->sizes[i] = sz;
     p->x_off[i + 1] = p->x_off[i] + len;
@@ -548,41 +711,21 @@ scd_status plan_create_exact(int32_t estimator, int32_t nsig, const int64_t* len
     if (ps != SCD_OK) { free_plan(p); return ps; }
   }
   layout_outputs(p);
-  p->ws_bytes = ws;
-  if (!(p->hamming = table_hamming(Np, &e)) || !(p->err = device_error_word(&e))) {
+  if (!(p->hamming = table_hamming(Np, &e)) || !(p->err = device_error_word(&e)) ||
+      !(p->tw_np = table_pass(Np, &e))) {
     free_plan(p);
     return cuda_status(e);
   }
+  if (precision == SCD_SPLIT_BF16 && !(p->bm_np = table_tc_bmats(Np, &p->bbytes_np, &e))) {
+    free_plan(p);
+    return cuda_status(e);
+  }
+  const scd_status bs = build_exact(p);
+  if (bs != SCD_OK) { free_plan(p); return bs; }
   *out = p;
   return SCD_OK;
 }
 
-// One exact-length run: per signal, the single-estimate stages on the shared workspace.
-cudaError_t run_exact(const scd_batch_plan* p, const float2* x, const float* w, float2* out, void* ws,
-                      cudaStream_t st) {
-  using namespace scd;
-  const int Np = p->Np, prec = p->precision;
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < p->nsig && e == cudaSuccess; ++i) {
-    const float2* xi = x + p->x_off[i];
-    float2* oi = out + p->out_off[i];
-    const int64_t sz = p->sizes[i];
-    if (p->estimator == 0) {
-      float2* X = (float2*)ws;
-      if ((e = fam_channelise(xi, Np, p->L, (int)sz, w, X, st, prec)) != cudaSuccess) break;
-      e = is_pow2(sz) ? fam_pair_fft(X, X, Np, (int)sz, oi, st, prec) : fam_pair_fft_any(X, X, Np, (int)sz, oi, st, prec);
-    } else if (is_pow2(sz)) {
-      if ((e = ssca_cdp(xi, xi, false, sz, Np, w, (float2*)ws, st, prec)) != cudaSuccess) break;
-      if ((e = ssca_cols((float2*)ws, sz, Np, st, prec)) != cudaSuccess) break;
-      e = ssca_rows((const float2*)ws, sz, Np, oi, st, prec);
-    } else {
-      if ((e = ssca_any_cdp(xi, xi, false, sz, Np, w, ws, st, prec)) != cudaSuccess) break;
-      if ((e = ssca_any_first(sz, Np, ws, st, prec)) != cudaSuccess) break;
-      e = ssca_any_second(sz, Np, ws, oi, st, prec);
-    }
-  }
-  return e;
-}
 }  // namespace
 
 extern "C" {
@@ -660,10 +803,6 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
   if (dev != p->device) return SCD_ERR_ARG;
   const float* w = window ? window : p->hamming;
   cudaStream_t st = (cudaStream_t)stream;
-  if (p->exact) {                                               // plain launches, no graph
-    e = run_exact(p, (const float2*)x_arena, w, (float2*)out_arena, workspace, st);
-    return e == cudaSuccess ? SCD_OK : cuda_status(e);
-  }
   BatchArgs A;
   A.tasks = p->d_tasks; A.ntasks = (int)p->tasks.size(); A.Np = p->Np; A.L = p->L; A.total = p->total;
   A.counters = p->d_counters; A.x = (const float2*)x_arena; A.y = A.x; A.conj = 0; A.pad_ = 0;

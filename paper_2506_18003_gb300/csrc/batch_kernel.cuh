@@ -15,7 +15,8 @@ struct Task {
   int32_t dep2, ch0;                      // second prerequisite (-1); SSCA: first channel of the unit
   int64_t first, tiles;                   // queue items [first, first + tiles)
   int64_t subtiles;                       // CTA tiles of the task; one queue item covers `per_item`
-  int32_t per_item, pad_;
+  int32_t per_item;
+  int32_t in_ws;                          // exact-length SSCA: channeliser inputs at xp_off / yp_off of ws
   int64_t x_off, out_off, ws_off;         // element offsets into the arenas
   int64_t mid_off;                        // SSCA: workspace offset of the unit's column-pass slot
   int32_t N, P, M1, M2;                   // the signal's sizes
@@ -23,6 +24,12 @@ struct Task {
   const float2* wN;                       // SSCA column pass: W_N^j
   const float2* cols;                     // SSCA column pass: W_N^{c m1'} at [m1'][c]
   const unsigned char* bmats;             // split form: B matrices of this size
+  // exact-length plans (batch_exact.cu)
+  int64_t xp_off, yp_off;                 // workspace offsets of the zero-padded channeliser inputs
+  int64_t ld;                             // row stride of the channeliser's output (0: N)
+                                          // (exact-length SSCA: t.P holds the padded length Npad_i)
+  const float2* chirp;                    // Bluestein chirp c[j] of the signal's length
+  const float2* bh;                       // Bluestein kernel spectrum (FAM: Bh; SSCA: row-ordered Bh)
 };
 
 struct BatchArgs {
@@ -279,9 +286,29 @@ cudaError_t launch_batch_profile(bool fam, bool tc, int grid, int smem, const Ba
 // the row pass / pair transforms reducing into alpha profiles.  Each launch runs a task list
 // whose tasks hold `first` and `subtiles` in CTA tiles; lists of kinds 1, 2, 4, 5 and 6 hold one
 // size class.
+// The task of CTA tile `tile` in a launch's task list: the last task whose first tile is <=
+// tile (binary search; one CTA tile per CTA).
+__device__ __forceinline__ int find_task(const Task* __restrict__ tl, int nt, int64_t tile) {
+  int lo = 0, hi = nt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&tl[mid].first) <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 cudaError_t staged_prepare(int kind, int M, int Np, bool tc, int* smem, int* per_sm);
 cudaError_t staged_launch(int kind, int M, int Np, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl,
                           int nt, int64_t total, cudaStream_t st);
+// The exact-length plans' own launch kinds (batch_exact.cu): 10 input preparation (chirp folded
+// into the channel-data product's second factor, zero padding), 11 / 13 the two Bluestein
+// column passes (M = M1), 12 the fused middle pass (M = M2), 14 the FAM pair transform of any
+// P (M = the cyclic length MM).
+cudaError_t exact_prepare(int kind, int M, int Np, bool tc, int* smem, int* per_sm);
+int exact_prep_per_tile();                                   // values of one signal per kind-10 CTA
+cudaError_t exact_launch(int kind, int M, int Np, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl,
+                         int nt, int64_t total, cudaStream_t st);
 
 }  // namespace bk
 }  // namespace scd

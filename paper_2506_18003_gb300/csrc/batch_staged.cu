@@ -18,17 +18,6 @@ namespace scd {
 namespace bk {
 namespace {
 
-// The task of CTA tile `tile`: the last task whose first tile is <= tile (binary search).
-__device__ __forceinline__ int find_task(const Task* __restrict__ tl, int nt, int64_t tile) {
-  int lo = 0, hi = nt - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(&tl[mid].first) <= tile) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 template <int NP, bool TC>
 __device__ __forceinline__ void st_cdp_cta(const BatchArgs& A, const Task* __restrict__ tl, int nt) {
   extern __shared__ __align__(128) float2 sm[];
@@ -41,8 +30,11 @@ __device__ __forceinline__ void st_cdp_cta(const BatchArgs& A, const Task* __res
     const int64_t tile = blockIdx.x;
     const Task& t = tl[find_task(tl, nt, tile)];
     const int64_t local = tile - t.first;
-    ssca_cdp_tile<NP, TC>(sm, ctx, A.x + t.x_off, A.y + t.x_off, A.conj != 0, t.N, A.window, A.tw_np, A.ws + t.ws_off,
-                          (int)local * TileShape<NP>::C, base + CdpStage<NP, TC>::off);
+    // exact-length plans: the zero-padded inputs with the chirp folded in sit in the workspace
+    const float2* xb = t.in_ws ? A.ws + t.xp_off : A.x + t.x_off;
+    const float2* yb = t.in_ws ? A.ws + t.yp_off : A.y + t.x_off;
+    ssca_cdp_tile<NP, TC>(sm, ctx, xb, yb, A.conj != 0, t.N, A.window, A.tw_np, A.ws + t.ws_off,
+                          (int)local * TileShape<NP>::C, base + CdpStage<NP, TC>::off, t.ld);
   }
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
@@ -293,6 +285,7 @@ bool valid(int kind, int M, bool tc) {
 }  // namespace
 
 cudaError_t staged_prepare(int kind, int M, int Np, bool tc, int* smem, int* per_sm) {
+  if (kind >= 10) return exact_prepare(kind, M, Np, tc, smem, per_sm);
   if (!valid(kind, M, tc)) return cudaErrorInvalidValue;
   if (kind == 7) {
     FusedSplit fs;
@@ -314,6 +307,7 @@ cudaError_t staged_prepare(int kind, int M, int Np, bool tc, int* smem, int* per
 
 cudaError_t staged_launch(int kind, int M, int Np, bool tc, int grid, int smem, const BatchArgs& A, const Task* tl,
                           int nt, int64_t total, cudaStream_t st) {
+  if (kind >= 10) return exact_launch(kind, M, Np, tc, grid, smem, A, tl, nt, total, st);
   if (!valid(kind, M, tc)) return cudaErrorInvalidValue;
   if (kind == 7) {
     FusedSplit fs;

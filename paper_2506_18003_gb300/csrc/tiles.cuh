@@ -113,11 +113,13 @@ struct CdpStage {
 template <int NP, bool TC>
 using CdpSmem = FftSmem<NP, TileShape<NP>::C, TileShape<NP>::NT, TC, CdpStage<NP, TC>::end>;
 
+// ld: row stride of X_g (0: N; exact-length plans lay X_g out in rows of the cyclic length)
 template <int NP, bool TC>
 __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ x,
                                               const float2* __restrict__ y, bool conj, int N,
                                               const float* __restrict__ a, const float2* __restrict__ tw,
-                                              float2* __restrict__ Xg, int n0, unsigned char* stage) {
+                                              float2* __restrict__ Xg, int n0, unsigned char* stage,
+                                              int64_t ld = 0) {
   using S = TileShape<NP>;
   float2* xs = reinterpret_cast<float2*>(stage);
   float* as = reinterpret_cast<float*>(stage + (S::C + NP) * 8);
@@ -138,7 +140,8 @@ __device__ __forceinline__ void ssca_cdp_tile(float2* sm, TcCtx& ctx, const floa
     const int r = (j - smod) & (NP - 1);                            // j = (s + r) mod Np
     return cscale(xs[c + r], as[r]);
   };
-  auto dst = [&](int, int f, float2 v) { o[(int64_t)((f + NP / 2) & (NP - 1)) * N] = cmulc(v, xn); };
+  const int64_t row = ld ? ld : N;
+  auto dst = [&](int, int f, float2 v) { o[(int64_t)((f + NP / 2) & (NP - 1)) * row] = cmulc(v, xn); };
   tile_fft<NP, S::C, true, false, S::NT, TC>(sm, tw, ctx, src, dst);
 }
 

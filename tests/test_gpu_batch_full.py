@@ -148,3 +148,73 @@ def test_ssca_batch_fused_profiles(torch):
         same = binding.scd_ssca_alpha_profile(est[i], N, Np)
         assert torch.equal(plan.output(prof, i), same), i
     plan.close()
+
+
+def _exact_lengths():
+    """40 lengths: powers of two, primes, one above and one below a power of two, and the
+    log-uniform mix of the headline workload."""
+    fixed = [4096, 8192, 65536, 4099, 8191, 10007, 65537, 131071, 131073, 200003]
+    return fixed + [int(v) for v in signals.batch_lengths(30, seed=4242)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_ssca_exact_batch_40_signals(torch, precision):
+    """Exact-length SSCA plan over 40 signals of mixed lengths (Bluestein for those that are
+    not powers of two), one graph: every signal equals the single-estimate call bit for bit;
+    the shortest and longest signal of each cyclic length against the FP64 oracle."""
+    Np = 128
+    lengths = _exact_lengths()
+    sigs = [signals.batch_signal(1000 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("ssca", lengths, Np, 1, precision, exact=True)
+    assert plan.sizes == lengths
+    out = _run(torch, plan, sigs)
+    a = orc.hamming_window(Np)
+    tol = FP32_TOL if precision == "fp32" else 1e-3
+    ad = torch.from_numpy(a).cuda()
+    cyc = [n if n & (n - 1) == 0 else 1 << (2 * n - 2).bit_length() for n in lengths]
+    ch = np.array([0, 31, 64, 127])
+    for c in sorted(set(cyc)):
+        idx = [i for i, v in enumerate(cyc) if v == c]
+        for i in sorted({idx[0], idx[-1]}):
+            est = plan.output(out, i)
+            single = binding.scd_ssca(torch.from_numpy(sigs[i]).cuda(), Np, window=ad, precision=precision,
+                                      schedule="stages")
+            assert torch.equal(est, single), i
+            ref = orc.ssca(sigs[i], a, Np, channels=ch, chunk=1 << 15)
+            got = est[torch.from_numpy(ch).cuda()].cpu().numpy()
+            smax = est.abs().max().item()
+            assert float(np.max(np.abs(got - ref))) / smax <= tol, (i, lengths[i])
+    plan.close()
+    del out
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_fam_exact_batch_40_signals(torch, precision):
+    """Exact-length FAM plan (P_i = (len_i - Np)//L + 1, Bluestein where P_i is not a power of
+    two) over 40 signals, one graph: sampled pairs of the shortest and longest signal of each
+    transform size against the FP64 oracle."""
+    Np, L = 64, 16
+    # P that is not a power of two runs both cyclic transforms inside one CTA: P <= 8192
+    lengths = [min(n, 8191 * L + Np) for n in _exact_lengths()]
+    sigs = [signals.batch_signal(1100 + i, n) for i, n in enumerate(lengths)]
+    plan = binding.BatchPlan("fam", lengths, Np, L, precision, exact=True)
+    assert plan.sizes == [(n - Np) // L + 1 for n in lengths]
+    out = _run(torch, plan, sigs)
+    a = orc.hamming_window(Np)
+    tol = FP32_TOL if precision == "fp32" else 1e-3
+    kh = np.array([0, 63, 31, 32, 5])
+    lh = np.array([0, 0, 32, 31, 60])
+    cls = [P if P & (P - 1) == 0 else -(1 << (2 * P - 2).bit_length()) for P in plan.sizes]
+    for c in sorted(set(cls)):
+        idx = [i for i, v in enumerate(cls) if v == c]
+        for i in sorted({idx[0], idx[-1]}):
+            P = plan.sizes[i]
+            est = plan.output(out, i)
+            ref = orc.fam_pairs(sigs[i], a, Np, L, P, kh, lh)
+            got = est[torch.from_numpy(kh).cuda(), torch.from_numpy(lh).cuda()].cpu().numpy()
+            smax = est.abs().max().item()
+            assert float(np.max(np.abs(got - ref))) / smax <= tol, (i, P)
+    plan.close()
+    del out
+    torch.cuda.empty_cache()
