@@ -26,6 +26,37 @@ namespace scd {
 // ----------------------------------------------------------------------------- complex
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The same sums with the packed two-lane FP32 instructions (add / sub .rn.f32x2): one
+// instruction for both components, each lane rounded exactly like the scalar add, so the results
+// are bit-identical.  Transforms opt in per call site (PK): it pays where the butterflies' adds
+// bound the kernel (the FAM pair transform: batch 17.19 -> 16.68 ms) and costs where the
+// register pairs it needs raise pressure (the fused SSCA's 1024-point second pass: +6%).
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+  return (unsigned long long)__float_as_uint(a.x) | ((unsigned long long)__float_as_uint(a.y) << 32);
+}
+__device__ __forceinline__ float2 f2_from(unsigned long long r) {
+  return make_float2(__uint_as_float((unsigned)r), __uint_as_float((unsigned)(r >> 32)));
+}
+#endif
+__host__ __device__ __forceinline__ float2 cadd_pk(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(r);
+#else
+  return cadd(a, b);
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub_pk(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return f2_from(r);
+#else
+  return csub(a, b);
+#endif
+}
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -106,27 +137,27 @@ __host__ __device__ __forceinline__ float2 twc(float2 d) {
   }
 }
 
-template <int R, int SPAN, int START, int J>
+template <int R, int SPAN, int START, int J, bool PK>
 __host__ __device__ __forceinline__ void dif_bfly(float2* v) {
   if constexpr (J < SPAN) {
     float2 a = v[START + J], b = v[START + J + SPAN];
-    v[START + J] = cadd(a, b);
-    v[START + J + SPAN] = twc<2 * SPAN, J>(csub(a, b));
-    dif_bfly<R, SPAN, START, J + 1>(v);
+    v[START + J] = PK ? cadd_pk(a, b) : cadd(a, b);
+    v[START + J + SPAN] = twc<2 * SPAN, J>(PK ? csub_pk(a, b) : csub(a, b));
+    dif_bfly<R, SPAN, START, J + 1, PK>(v);
   }
 }
-template <int R, int SPAN, int START>
+template <int R, int SPAN, int START, bool PK>
 __host__ __device__ __forceinline__ void dif_stage(float2* v) {
   if constexpr (START < R) {
-    dif_bfly<R, SPAN, START, 0>(v);
-    dif_stage<R, SPAN, START + 2 * SPAN>(v);
+    dif_bfly<R, SPAN, START, 0, PK>(v);
+    dif_stage<R, SPAN, START + 2 * SPAN, PK>(v);
   }
 }
-template <int R, int SPAN>
+template <int R, int SPAN, bool PK>
 __host__ __device__ __forceinline__ void dif_all(float2* v) {
   if constexpr (SPAN >= 1) {
-    dif_stage<R, SPAN, 0>(v);
-    dif_all<R, SPAN / 2>(v);
+    dif_stage<R, SPAN, 0, PK>(v);
+    dif_all<R, SPAN / 2, PK>(v);
   }
 }
 __host__ __device__ constexpr int bitrev(int i, int R) {
@@ -143,10 +174,10 @@ __host__ __device__ __forceinline__ void unscramble(float2* v) {
   }
 }
 // In-register R-point forward DFT, natural order in and out (radix-2 DIF network).
-template <int R>
+template <int R, bool PK = false>
 __host__ __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R > 1) {
-    dif_all<R, R / 2>(v);
+    dif_all<R, R / 2, PK>(v);
     unscramble<R, 0>(v);
   }
 }
@@ -170,8 +201,9 @@ __host__ __device__ inline int64_t pass_twiddle_exponent(int e, int M, int r0, i
 }
 
 // Per-thread pieces of the batched transform; registers v[] persist between pieces and
-// the caller separates the pieces that touch shared memory with barriers.
-template <int M>
+// the caller separates the pieces that touch shared memory with barriers.  PK: the radix DFTs'
+// complex sums with the packed two-lane instructions (bit-identical results).
+template <int M, bool PK = false>
 struct FftPieces {
   using PI = PlanInfo<M>;
   static constexpr int E = PI::E, T = PI::T;
@@ -182,7 +214,7 @@ struct FftPieces {
     constexpr int R = PI::r0;
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src(c, t + r * (M / R));
-    dft<R>(v);
+    dft<R, PK>(v);
   }
   // pass 0 outputs of thread t to shared memory (A_{r0}[t, j] at j + t r0)
   __host__ __device__ __forceinline__ static void pass0_store(int t, float2* reg, const float2* v) {
@@ -205,7 +237,7 @@ struct FftPieces {
         if (r > 0) x = cmul(x, TWS ? tw[PI::off(S) + r * p + k] : SCD_LDG(tw + PI::off(S) + r * p + k));
         v[b * R + r] = x;
       }
-      dft<R>(v + b * R);
+      dft<R, PK>(v + b * R);
     }
   }
   // pass S outputs to shared memory (not the last pass)
@@ -266,11 +298,11 @@ __device__ __forceinline__ void team_sync() {
 // SYNC_DST: put a CTA barrier between the last pass's shared-memory reads and the dst
 // calls, for consumers that stage outputs in the same shared memory.  Callers that loop
 // over several batches must also barrier between batches.
-template <int M, int C, bool CFAST, bool SYNC_DST, class Src, class Dst>
+template <int M, int C, bool CFAST, bool SYNC_DST, bool PK = false, class Src, class Dst>
 __device__ __forceinline__ void fft_batch(float2* __restrict__ sm, const float2* __restrict__ tw,
                                           Src& src, Dst& dst) {
   using PI = PlanInfo<M>;
-  using F = FftPieces<M>;
+  using F = FftPieces<M, PK>;
   constexpr int E = PI::E, T = PI::T;
   const int tid = threadIdx.x;
   const int c = CFAST ? (tid % C) : (tid / T);

@@ -23,10 +23,10 @@ __device__ __forceinline__ void profile_max(unsigned* p, unsigned v) { atomicMax
 
 // Runs the C transforms of one tile in the requested form; for TC the caller has opened the
 // tensor-core context and loaded the B matrices of size M into ctx.bsm.
-template <int M, int C, bool CFAST, bool SYNC_DST, int THREADS, bool TC, class Src, class Dst>
+template <int M, int C, bool CFAST, bool SYNC_DST, int THREADS, bool TC, bool PK = false, class Src, class Dst>
 __device__ __forceinline__ void tile_fft(float2* sm, const float2* __restrict__ tw, TcCtx& ctx, Src& src, Dst& dst) {
   if constexpr (TC) fft_batch_tc<M, C, CFAST, SYNC_DST, THREADS>(sm, tw, src, dst, ctx);
-  else fft_batch<M, C, CFAST, SYNC_DST>(sm, tw, src, dst);
+  else fft_batch<M, C, CFAST, SYNC_DST, PK>(sm, tw, src, dst);
 }
 
 // ---------------------------------------------------------------- FAM channeliser (K1)
@@ -89,7 +89,7 @@ __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const flo
       if (valid) o[(f + PP / 2) & (PP - 1)] = v;
     }
   };
-  tile_fft<PP, S::C, false, false, S::NT, TC>(sm, tw, ctx, src, dst);
+  tile_fft<PP, S::C, false, false, S::NT, TC, true>(sm, tw, ctx, src, dst);   // packed sums (FP32 form)
 }
 
 // ---------------------------------------------------------------- SSCA channeliser + CDP (K3)

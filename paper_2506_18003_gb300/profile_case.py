@@ -31,15 +31,14 @@ def main() -> int:
     ap.add_argument("--P", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", default="fp32")
-    ap.add_argument("--schedule", default="auto", help="ssca, batch_ssca: auto, stages, persistent or fused")
+    ap.add_argument("--schedule", default="auto", help="ssca, batch_*: auto, stages, persistent or fused (SSCA)")
     a = ap.parse_args()
 
     if a.estimator.startswith("batch_"):
         est = a.estimator[6:]
         lengths = [int(v) for v in signals.batch_lengths(a.nsig)]
         plan = binding.BatchPlan(est, lengths, a.Np, a.L, a.precision)
-        if est == "ssca":
-            plan.set_schedule(a.schedule)
+        plan.set_schedule(a.schedule)
         xa = torch.from_numpy(signals.awgn(int(sum(lengths)), seed=99)).cuda()
         out = torch.empty(plan.out_offsets[-1], dtype=torch.complex64, device="cuda")
         ws = torch.empty(max(1, plan.workspace_bytes), dtype=torch.uint8, device="cuda")
