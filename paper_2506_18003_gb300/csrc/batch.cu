@@ -207,7 +207,7 @@ scd_status build_tasks(scd_batch_plan* p) {
       Task t = T[stage0[i]];
       t.op = OP_FAM_PAIRS; t.size = (int)sz; t.dep = stage0[i];
       const int c = tile_c((int)sz);
-      t.tiles = ((int64_t)Np * Np + c - 1) / c;
+      t.tiles = (fam_pair_count<0>(Np, true) + c - 1) / c;      // the pairs kh <= lh (auto estimate)
       if (!(t.tw = table_pass((int)sz, &e))) { return cuda_status(e); }
       if (tc && !(t.bmats = table_tc_bmats((int)sz, &t.bbytes, &e))) { return cuda_status(e); }
       add(t);
@@ -333,7 +333,7 @@ scd_status build_tasks(scd_batch_plan* p) {
         if (p->sizes[i] != P) continue;
         Task t = stage0_task(i);
         t.size = (int)P;
-        t.subtiles = ((int64_t)Np * Np + tile_c((int)P) - 1) / tile_c((int)P);
+        t.subtiles = (fam_pair_count<0>(Np, true) + tile_c((int)P) - 1) / tile_c((int)P);   // pairs kh <= lh
         if (!(t.tw = table_pass((int)P, &e))) return cuda_status(e);
         if (tc && !(t.bmats = table_tc_bmats((int)P, &t.bbytes, &e))) return cuda_status(e);
         p->st_tasks.push_back(t);
@@ -569,7 +569,7 @@ scd_status build_exact(scd_batch_plan* p) {
         t.P = (int)P;
         t.size = M;
         t.ws_off = ws[i];
-        t.subtiles = ((int64_t)Np * Np + tile_c(M) - 1) / tile_c(M);
+        t.subtiles = (fam_pair_count<0>(Np, cls > 0) + tile_c(M) - 1) / tile_c(M);   // kind 4: pairs kh <= lh
         if (!(t.tw = table_pass(M, &e))) return cuda_status(e);
         if (cls < 0 && (!(t.chirp = table_chirp(P, &e)) || !(t.bh = table_bluestein(P, M, &e)))) return cuda_status(e);
         if (tc && !(t.bmats = table_tc_bmats(M, &t.bbytes, &e))) return cuda_status(e);

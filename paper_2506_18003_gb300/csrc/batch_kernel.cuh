@@ -146,7 +146,7 @@ __device__ __forceinline__ void fam_tile(const BatchArgs& A, const Task& t, int6
     float* prof = PROF ? reinterpret_cast<float*>(A.out) + t.out_off : nullptr;
     const int PL = t.P * A.L, Q = PL / A.Np;
     switch (t.P) {
-#define SCD_PR(PV) case PV: fam_pairs_tile<PV, TC, PROF>(sm, ctx, X, X, A.Np, out, t.tw, tile * TileShape<PV>::C, prof, PL, Q, A.prof_power); break;
+#define SCD_PR(PV) case PV: fam_pairs_tile<PV, TC, PROF, true>(sm, ctx, X, X, A.Np, out, t.tw, tile * TileShape<PV>::C, prof, PL, Q, A.prof_power); break;
       SCD_PR(2) SCD_PR(4) SCD_PR(8) SCD_PR(16) SCD_PR(32) SCD_PR(64) SCD_PR(128) SCD_PR(256) SCD_PR(512)
       SCD_PR(1024) SCD_PR(2048) SCD_PR(4096) SCD_PR(8192)
 #undef SCD_PR

@@ -181,10 +181,10 @@ __global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC>()) k_st_fpairs(B
     const float2* X = A.ws + t.ws_off;
     if constexpr (PROF) {
       const int PL = t.P * A.L;
-      fam_pairs_tile<PP, TC, true>(sm, ctx, X, X, A.Np, nullptr, t.tw, (tile - t.first) * S::C,
+      fam_pairs_tile<PP, TC, true, true>(sm, ctx, X, X, A.Np, nullptr, t.tw, (tile - t.first) * S::C,
                                    reinterpret_cast<float*>(A.out) + t.out_off, PL, PL / A.Np, A.prof_power);
     } else {
-      fam_pairs_tile<PP, TC, false>(sm, ctx, X, X, A.Np, A.out + t.out_off, t.tw, (tile - t.first) * S::C);
+      fam_pairs_tile<PP, TC, false, true>(sm, ctx, X, X, A.Np, A.out + t.out_off, t.tw, (tile - t.first) * S::C);
     }
   }
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);

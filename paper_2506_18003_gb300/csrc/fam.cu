@@ -35,7 +35,9 @@ k_fam_channelise(const float2* __restrict__ x, int L, int P, const float* __rest
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int PP, bool TC>
+// SYM: the auto estimate (Y = X): only the pairs kh <= lh are transformed, each writing both
+// rows (fam_pairs_tile)
+template <int PP, bool TC, bool SYM>
 __device__ __forceinline__ void fam_pairs_cta(const float2* __restrict__ X, const float2* __restrict__ Y, int Np,
                                               float2* __restrict__ out, const float2* __restrict__ tw,
                                               const unsigned char* __restrict__ bmats, unsigned* err) {
@@ -45,23 +47,23 @@ __device__ __forceinline__ void fam_pairs_cta(const float2* __restrict__ X, cons
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  fam_pairs_tile<PP, TC>(sm, ctx, X, Y, Np, out, tw, (int64_t)blockIdx.x * S::C);
+  fam_pairs_tile<PP, TC, false, SYM>(sm, ctx, X, Y, Np, out, tw, (int64_t)blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-template <int PP, bool TC>
+template <int PP, bool TC, bool SYM>
 __global__ void __launch_bounds__(TileShape<PP>::NT)
 k_fam_pairs(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, float2* __restrict__ out,
             const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
-  fam_pairs_cta<PP, TC>(X, Y, Np, out, tw, bmats, err);
+  fam_pairs_cta<PP, TC, SYM>(X, Y, Np, out, tw, bmats, err);
 }
 
 // The same kernel with its registers capped so that MINB CTAs share an SM.
-template <int PP, bool TC, int MINB>
+template <int PP, bool TC, bool SYM, int MINB>
 __global__ void __launch_bounds__(TileShape<PP>::NT, MINB)
 k_fam_pairs_capped(const float2* __restrict__ X, const float2* __restrict__ Y, int Np, float2* __restrict__ out,
                    const float2* __restrict__ tw, const unsigned char* __restrict__ bmats, unsigned* err) {
-  fam_pairs_cta<PP, TC>(X, Y, Np, out, tw, bmats, err);
+  fam_pairs_cta<PP, TC, SYM>(X, Y, Np, out, tw, bmats, err);
 }
 
 template <class K>
@@ -93,23 +95,31 @@ template <> struct FamPairsBlocks<2048, false> { static constexpr int value = 4;
 template <> struct FamPairsBlocks<4096, false> { static constexpr int value = 4; };
 template <> struct FamPairsBlocks<8192, false> { static constexpr int value = 2; };
 
-template <int PV, bool TC>
+template <int PV, bool TC, bool SYM>
 auto fam_pairs_kernel() {
-  if constexpr (FamPairsBlocks<PV, TC>::value > 0) return k_fam_pairs_capped<PV, TC, FamPairsBlocks<PV, TC>::value>;
-  else return k_fam_pairs<PV, TC>;
+  if constexpr (FamPairsBlocks<PV, TC>::value > 0) return k_fam_pairs_capped<PV, TC, SYM, FamPairsBlocks<PV, TC>::value>;
+  else return k_fam_pairs<PV, TC, SYM>;
 }
 
+template <int PV, bool TC, bool SYM>
+cudaError_t launch_k2_t(const float2* X, const float2* Y, int Np, float2* out, const float2* tw,
+                        const unsigned char* bm, unsigned* err, cudaStream_t st) {
+  using S = TileShape<PV>;
+  constexpr int sm = FftSmem<PV, S::C, S::NT, TC>::total;
+  auto kernel = fam_pairs_kernel<PV, TC, SYM>();
+  cudaError_t e = set_smem(kernel, sm);
+  if (e != cudaSuccess) return e;
+  const int64_t npairs = fam_pair_count<PV>(Np, SYM);
+  kernel<<<(unsigned)((npairs + S::C - 1) / S::C), S::NT, sm, st>>>(X, Y, Np, out, tw, bm, err);
+  return cudaGetLastError();
+}
+
+// The auto estimate (Y is X) transforms the pairs kh <= lh only.
 template <int PV, bool TC>
 cudaError_t launch_k2(const float2* X, const float2* Y, int Np, float2* out, const float2* tw, const unsigned char* bm,
                       unsigned* err, cudaStream_t st) {
-  using S = TileShape<PV>;
-  constexpr int sm = FftSmem<PV, S::C, S::NT, TC>::total;
-  auto kernel = fam_pairs_kernel<PV, TC>();
-  cudaError_t e = set_smem(kernel, sm);
-  if (e != cudaSuccess) return e;
-  const int64_t npairs = (int64_t)Np * Np;
-  kernel<<<(unsigned)((npairs + S::C - 1) / S::C), S::NT, sm, st>>>(X, Y, Np, out, tw, bm, err);
-  return cudaGetLastError();
+  return X == Y ? launch_k2_t<PV, TC, true>(X, Y, Np, out, tw, bm, err, st)
+                : launch_k2_t<PV, TC, false>(X, Y, Np, out, tw, bm, err, st);
 }
 
 template <bool TC>

@@ -59,9 +59,20 @@ __device__ __forceinline__ void fam_channelise_tile(float2* sm, TcCtx& ctx, cons
 //   out[kh][lh][qh] = sum_p X[kh][p] conj(Y[lh][p]) W_P^{(q p) mod P}
 // Y = X for the auto estimate, the partner's channeliser output for a cross estimate, and
 // the conjugated one for a conjugate estimate.
+// SYM (auto estimate, Y = X): the pair products are conjugate-symmetric, z_lk(p) = conj(z_kl(p)),
+// so S(l, k, -q) = conj(S(k, l, q)) exactly; only the Np (Np + 1) / 2 pairs with kh <= lh are
+// transformed and each writes both rows (the mirrored one at qh' = (P/2 - f) mod P for natural
+// bin f).  The pairs are enumerated over a folded triangle: pair = r (Np + 1) + c, r < Np/2, is
+// (r, r + c) for c < Np - r and (Np - 1 - r, c - 1) otherwise (rows r and Np - 1 - r of the
+// triangle together hold Np + 1 pairs).
 // PROF: instead of storing S, every kept bin (q in [-Q, Q)) is reduced into the alpha profile
 // prof[ah], ah = (k - l) Q + q + P L, by profile_max of |S|^power.
-template <int PP, bool TC, bool PROF = false>
+template <int PP>
+__host__ __device__ inline int64_t fam_pair_count(int Np, bool sym) {
+  return sym ? (int64_t)Np * (Np + 1) / 2 : (int64_t)Np * Np;
+}
+
+template <int PP, bool TC, bool PROF = false, bool SYM = false>
 __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X,
                                                const float2* __restrict__ Y, int Np, float2* __restrict__ out,
                                                const float2* __restrict__ tw, int64_t pair0, float* prof = nullptr,
@@ -69,24 +80,38 @@ __device__ __forceinline__ void fam_pairs_tile(float2* sm, TcCtx& ctx, const flo
   using S = TileShape<PP>;
   // this thread's pair (transforms are t-fast: c = tid / T), resolved once
   const int64_t pair = pair0 + (int)threadIdx.x / S::T;
-  const bool valid = pair < (int64_t)Np * Np;
-  const int kh = valid ? (int)(pair / Np) : 0, lh = valid ? (int)(pair % Np) : 0;
+  const bool valid = pair < fam_pair_count<PP>(Np, SYM);
+  int kh = 0, lh = 0;
+  if (valid) {
+    if constexpr (SYM) {
+      const int r = (int)(pair / (Np + 1)), c = (int)(pair % (Np + 1));
+      if (c < Np - r) { kh = r; lh = r + c; }
+      else { kh = Np - 1 - r; lh = c - 1; }
+    } else {
+      kh = (int)(pair / Np);
+      lh = (int)(pair % Np);
+    }
+  }
+  const bool mirror = SYM && kh != lh;
   const float2* __restrict__ xk = X + (int64_t)kh * PP;
   const float2* __restrict__ xl = Y + (int64_t)lh * PP;
-  float2* __restrict__ o = PROF ? nullptr : out + pair * PP;
+  float2* __restrict__ o = PROF ? nullptr : out + ((int64_t)kh * Np + lh) * PP;
+  float2* __restrict__ om = PROF ? nullptr : out + ((int64_t)lh * Np + kh) * PP;
   auto src = [&](int, int p) -> float2 {
     return valid ? cmulc(__ldg(xk + p), __ldg(xl + p)) : make_float2(0.f, 0.f);
   };
   auto dst = [&](int, int f, float2 v) {
     if constexpr (PROF) {
       const int q = ((f + PP / 2) & (PP - 1)) - PP / 2;
-      if (valid && q >= -Q && q < Q) {
-        const float m2 = fmaf(v.x, v.x, v.y * v.y);
-        profile_max(reinterpret_cast<unsigned*>(prof) + ((kh - lh) * Q + q + PL),
-                    __float_as_uint(power == 2 ? m2 : sqrtf(m2)));
-      }
+      const float m2 = fmaf(v.x, v.x, v.y * v.y);
+      const unsigned val = __float_as_uint(power == 2 ? m2 : sqrtf(m2));
+      if (valid && q >= -Q && q < Q)
+        profile_max(reinterpret_cast<unsigned*>(prof) + ((kh - lh) * Q + q + PL), val);
+      if (mirror && -q >= -Q && -q < Q)                  // S(l, k, -q): the same magnitude
+        profile_max(reinterpret_cast<unsigned*>(prof) + ((lh - kh) * Q - q + PL), val);
     } else {
       if (valid) o[(f + PP / 2) & (PP - 1)] = v;
+      if (mirror) om[(PP / 2 - f) & (PP - 1)] = cconj(v);
     }
   };
   tile_fft<PP, S::C, false, false, S::NT, TC, true>(sm, tw, ctx, src, dst);   // packed sums (FP32 form)
