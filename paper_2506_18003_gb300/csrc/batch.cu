@@ -569,7 +569,7 @@ scd_status build_exact(scd_batch_plan* p) {
         t.P = (int)P;
         t.size = M;
         t.ws_off = ws[i];
-        t.subtiles = (fam_pair_count<0>(Np, cls > 0) + tile_c(M) - 1) / tile_c(M);   // kind 4: pairs kh <= lh
+        t.subtiles = (fam_pair_count<0>(Np, true) + tile_c(M) - 1) / tile_c(M);   // pairs kh <= lh
         if (!(t.tw = table_pass(M, &e))) return cuda_status(e);
         if (cls < 0 && (!(t.chirp = table_chirp(P, &e)) || !(t.bh = table_bluestein(P, M, &e)))) return cuda_status(e);
         if (tc && !(t.bmats = table_tc_bmats(M, &t.bbytes, &e))) return cuda_status(e);

@@ -122,8 +122,8 @@ __device__ __forceinline__ void ex_fpairs_cta(const BatchArgs& A, const Task* __
     const int64_t tile = blockIdx.x;
     const Task& t = tl[find_task(tl, nt, tile)];
     const float2* X = A.ws + t.ws_off;
-    fam_pairs_any_tile<MM, TC>(sm, ctx, X, X, A.Np, t.P, A.out + t.out_off, t.tw, t.chirp, t.bh,
-                               (tile - t.first) * S::C);
+    fam_pairs_any_tile<MM, TC, true>(sm, ctx, X, X, A.Np, t.P, A.out + t.out_off, t.tw, t.chirp, t.bh,
+                                     (tile - t.first) * S::C);
   }
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }

@@ -57,7 +57,9 @@ __device__ __forceinline__ void fam_pairs_any_cta(const float2* __restrict__ X, 
   unsigned char* base = reinterpret_cast<unsigned char*>(sm);
   TcCtx ctx{};
   if constexpr (TC) ctx = tc_begin<FS::tmem_cols>(base + FS::region0 + FS::bbytes, base + FS::region0, bmats, FS::bbytes, err);
-  fam_pairs_any_tile<MM, TC>(sm, ctx, X, Y, Np, P, out, tw, chirp, bh, (int64_t)blockIdx.x * S::C);
+  // the auto estimate (Y is X): the pairs kh <= lh, both rows from each
+  if (X == Y) fam_pairs_any_tile<MM, TC, true>(sm, ctx, X, Y, Np, P, out, tw, chirp, bh, (int64_t)blockIdx.x * S::C);
+  else fam_pairs_any_tile<MM, TC, false>(sm, ctx, X, Y, Np, P, out, tw, chirp, bh, (int64_t)blockIdx.x * S::C);
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
@@ -84,7 +86,7 @@ cudaError_t launch_fam_any_k(K kernel, int smem, int NT, int C, const float2* X,
                              cudaStream_t st) {
   cudaError_t e = set_smem(kernel, smem);
   if (e != cudaSuccess) return e;
-  const int64_t npairs = (int64_t)Np * Np;
+  const int64_t npairs = X == Y ? (int64_t)Np * (Np + 1) / 2 : (int64_t)Np * Np;     // auto estimate: kh <= lh
   kernel<<<(unsigned)((npairs + C - 1) / C), NT, smem, st>>>(X, Y, Np, P, out, tw, chirp, bh, t.bm, t.err);
   return cudaGetLastError();
 }

@@ -74,7 +74,9 @@ using ResidentSmem = FftSmem<M, TileShape<M>::C, TileShape<M>::NT, TC, TileShape
 // pairs pair0 .. pair0 + C - 1 (pair = kh Np + lh), P < MM <= 2P - 1 rounded up to a power of 2:
 //   out[kh][lh][qh] = sum_{p<P} X[kh][p] conj(Y[lh][p]) W_P^{(q p) mod P},  qh = (q + P/2) mod P
 // (q in natural order; for odd P the zero bin is stored at floor(P/2)).  X and Y rows are P long.
-template <int MM, bool TC>
+// SYM (auto estimate, Y = X): the pairs kh <= lh only, each writing its row and the mirrored row
+// S(l, k, -q) = conj S(k, l, q), as fam_pairs_tile (tiles.cuh).
+template <int MM, bool TC, bool SYM = false>
 __device__ __forceinline__ void fam_pairs_any_tile(float2* sm, TcCtx& ctx, const float2* __restrict__ X,
                                                    const float2* __restrict__ Y, int Np, int P,
                                                    float2* __restrict__ out, const float2* __restrict__ tw,
@@ -84,11 +86,23 @@ __device__ __forceinline__ void fam_pairs_any_tile(float2* sm, TcCtx& ctx, const
   using PI = PlanInfo<MM>;
   const int c = (int)threadIdx.x / S::T;
   const int64_t pair = pair0 + c;
-  const bool valid = pair < (int64_t)Np * Np;
-  const int kh = valid ? (int)(pair / Np) : 0, lh = valid ? (int)(pair % Np) : 0;
+  const bool valid = pair < (SYM ? (int64_t)Np * (Np + 1) / 2 : (int64_t)Np * Np);
+  int kh = 0, lh = 0;
+  if (valid) {
+    if constexpr (SYM) {
+      const int r = (int)(pair / (Np + 1)), cc = (int)(pair % (Np + 1));
+      if (cc < Np - r) { kh = r; lh = r + cc; }
+      else { kh = Np - 1 - r; lh = cc - 1; }
+    } else {
+      kh = (int)(pair / Np);
+      lh = (int)(pair % Np);
+    }
+  }
+  const bool mirror = SYM && valid && kh != lh;
   const float2* __restrict__ xk = X + (int64_t)kh * P;
   const float2* __restrict__ xl = Y + (int64_t)lh * P;
-  float2* __restrict__ o = out + pair * P;
+  float2* __restrict__ o = out + ((int64_t)kh * Np + lh) * P;
+  float2* __restrict__ om = out + ((int64_t)lh * Np + kh) * P;
   float2* reg = sm + c * PI::stride(S::C);
   auto src1 = [&](int, int p) -> float2 {
     return (valid && p < P) ? cmul(cmulc(__ldg(xk + p), __ldg(xl + p)), __ldg(chirp + p)) : make_float2(0.f, 0.f);
@@ -99,8 +113,13 @@ __device__ __forceinline__ void fam_pairs_any_tile(float2* sm, TcCtx& ctx, const
   const int half = P / 2;
   auto dst2 = [&](int, int f, float2 v) {
     if (valid && f < P) {
+      const float2 s = cmulc(__ldg(chirp + f), v);
       const int qh = f + half < P ? f + half : f + half - P;
-      o[qh] = cmulc(__ldg(chirp + f), v);
+      o[qh] = s;
+      if (mirror) {                                      // bin -q of the mirrored pair
+        const int fm = f == 0 ? 0 : P - f;
+        om[fm + half < P ? fm + half : fm + half - P] = cconj(s);
+      }
     }
   };
   fft_resident<MM, S::C, S::NT, TC>(sm, tw, ctx, dst2);
