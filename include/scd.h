@@ -62,8 +62,8 @@ typedef enum { SCD_FP32 = 0, SCD_SPLIT_BF16 = 1 } scd_precision;
  * FUSED: two kernels: the channeliser, the channel-data product and the strip transform's
  *   first pass in one (the product X_g never leaves the chip), the second pass in the other.
  *   Where its tiles do not fit the sizes (FP32 form; Np in {64, 128, 256}, N = M1 M2 with
- *   M1 = 64 or 128, Np <= M2 <= 1024: e.g. N = 2^13..2^17 at Np = 128, 2^14..2^16 at
- *   Np = 256), the call runs the STAGES kernels instead.
+ *   M1 = 64, 128 or 256, Np <= M2 <= 2048: N = 2^12..2^19 at Np = 64, 2^13..2^19 at
+ *   Np = 128, 2^14..2^18 at Np = 256), the call runs the STAGES kernels instead.
  * AUTO: the choice scd_ssca_tune measured fastest for (N, Np, precision) on this GPU model
  *   (in this process, or from the SCD_TUNE_CACHE file); if never tuned, FUSED where it fits,
  *   else STAGES. */

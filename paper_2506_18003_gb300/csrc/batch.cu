@@ -351,7 +351,7 @@ scd_status build_tasks(scd_batch_plan* p) {
             Task t = stage0_task(i);
             t.M1 = fs.M1; t.M2 = fs.M2;
             t.size = kind == 7 ? fs.M1 : fs.M2;
-            t.subtiles = kind == 7 ? (int64_t)fs.M2 * fs.Q : (int64_t)Np * (fs.M1 / tile_c(fs.M2));
+            t.subtiles = kind == 7 ? (int64_t)fs.M2 * fs.Q : (int64_t)Np * (fs.M1 / rowsf_c(fs.M2));
             if (!(t.tw = table_pass(t.size, &e))) return cuda_status(e);
             if (kind == 7 && !(t.wN = table_roots((int)N, &e))) return cuda_status(e);
             p->st_tasks.push_back(t);

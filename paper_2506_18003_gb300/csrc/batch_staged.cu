@@ -122,10 +122,10 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kThreads, 2)
 // ... and tile B = the M2-point pass over m2 for C consecutive q1 of one channel; PROF: each
 // bin reduced into the signal's alpha profile instead of stored.
 template <int M2, bool PROF>
-__global__ void __launch_bounds__(kThreads, M2 >= 1024 ? 2 : 3)
+__global__ void __launch_bounds__(rowsf_threads(M2), M2 >= 1024 ? 2 : 3)
     k_st_sfb(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
   extern __shared__ __align__(128) float2 sm[];
-  constexpr int C = TileShape<M2>::C;
+  constexpr int C = rowsf_c(M2);
   const int64_t tile = blockIdx.x;
   const Task& t = tl[find_task(tl, nt, tile)];
   const int64_t local = tile - t.first;
@@ -228,9 +228,10 @@ cudaError_t prep_m(int kind, int* smem, int* per_sm) {
     if (kind == 4) return prepare_t(k_st_fpairs<M, TC, false>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
     if (kind == 6) return prepare_t(k_st_fpairs<M, TC, true>, FftSmem<M, S::C, S::NT, TC>::total, TC, smem, per_sm);
   }
-  if constexpr (M >= 64 && M <= 1024 && !TC) {
-    if (kind == 8) return prepare_t(k_st_sfb<M, false>, FftSmem<M, TileShape<M>::C, kThreads, false>::total, false, smem, per_sm);
-    if (kind == 9) return prepare_t(k_st_sfb<M, true>, FftSmem<M, TileShape<M>::C, kThreads, false>::total, false, smem, per_sm);
+  if constexpr (M >= 64 && M <= 2048 && !TC) {
+    using SB = TileShape<M, rowsf_threads(M)>;
+    if (kind == 8) return prepare_t(k_st_sfb<M, false>, FftSmem<M, SB::C, SB::NT, false>::total, false, smem, per_sm);
+    if (kind == 9) return prepare_t(k_st_sfb<M, true>, FftSmem<M, SB::C, SB::NT, false>::total, false, smem, per_sm);
   }
   if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) return prepare_t(k_st_cols<M, TC>, ColsSmem<M, TC>::total, TC, smem, per_sm);
@@ -257,9 +258,9 @@ void launch_m(int kind, int grid, int smem, const BatchArgs& A, const Task* tl, 
     if (kind == 4) k_st_fpairs<M, TC, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
     if (kind == 6) k_st_fpairs<M, TC, true><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
   }
-  if constexpr (M >= 64 && M <= 1024 && !TC) {
-    if (kind == 8) k_st_sfb<M, false><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
-    if (kind == 9) k_st_sfb<M, true><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
+  if constexpr (M >= 64 && M <= 2048 && !TC) {
+    if (kind == 8) k_st_sfb<M, false><<<grid, rowsf_threads(M), smem, st>>>(A, tl, nt, total);
+    if (kind == 9) k_st_sfb<M, true><<<grid, rowsf_threads(M), smem, st>>>(A, tl, nt, total);
   }
   if constexpr (M >= 64 && M <= 1024) {
     if (kind == 1) k_st_cols<M, TC><<<grid, kThreads, smem, st>>>(A, tl, nt, total);
@@ -278,7 +279,7 @@ bool valid(int kind, int M, bool tc) {
   if (kind == 0 || kind == 3) return pow2 && M >= 16 && M <= 256;
   if (kind == 4 || kind == 6) return pow2 && M <= 8192;
   if (kind == 7) return !tc;
-  if (kind == 8 || kind == 9) return !tc && pow2 && M >= 64 && M <= 1024;
+  if (kind == 8 || kind == 9) return !tc && pow2 && M >= 64 && M <= 2048;
   return pow2 && M >= 64 && M <= 1024 && kind >= 1 && kind <= 5;
 }
 

@@ -20,11 +20,11 @@ k_sf_chancol(const float2* __restrict__ x, const float2* __restrict__ y, int con
 
 // three CTAs per SM below M2 = 1024 (80 registers without spills); two at 1024
 template <int M2>
-__global__ void __launch_bounds__(256, M2 >= 1024 ? 2 : 3)
+__global__ void __launch_bounds__(rowsf_threads(M2), M2 >= 1024 ? 2 : 3)
 k_sf_rows(const float2* __restrict__ Y, int N, int M1, const float2* __restrict__ tw, float2* __restrict__ out) {
   extern __shared__ __align__(128) float2 sm[];
   const int64_t kh = blockIdx.y;
-  ssca_rowsf_tile<M2>(sm, Y + kh * N, out + kh * N, M1, tw, (int)blockIdx.x * TileShape<M2>::C);
+  ssca_rowsf_tile<M2>(sm, Y + kh * N, out + kh * N, M1, tw, (int)blockIdx.x * rowsf_c(M2));
 }
 
 template <class K>
@@ -47,7 +47,7 @@ cudaError_t launch_chancol_t(const float2* x, const float2* y, int conj, int N, 
 
 template <int M2>
 cudaError_t launch_rowsf_t(const float2* Y, int N, int Np, int M1, float2* out, cudaStream_t st) {
-  using S = TileShape<M2>;
+  using S = TileShape<M2, rowsf_threads(M2)>;
   constexpr int smem = FftSmem<M2, S::C, S::NT, false>::total;
   cudaError_t e;
   const float2* tw = table_pass(M2, &e);
@@ -90,6 +90,7 @@ cudaError_t ssca_fused_rows(const float2* ws, int64_t N, int Np, float2* out, cu
     case 256: return launch_rowsf_t<256>(ws, (int)N, Np, s.M1, out, st);
     case 512: return launch_rowsf_t<512>(ws, (int)N, Np, s.M1, out, st);
     case 1024: return launch_rowsf_t<1024>(ws, (int)N, Np, s.M1, out, st);
+    case 2048: return launch_rowsf_t<2048>(ws, (int)N, Np, s.M1, out, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -28,23 +28,25 @@
 namespace scd {
 
 // The fused split of an SSCA strip transform, or false where the tiles do not fit:
-// M1 = max(64, N / 1024) (so M2 <= 1024 fits the second pass's tile), Q = Np M1 / 8192 CTAs per
-// cluster (the block X_g(., k) takes 64 KB of shared memory per CTA, two CTAs per SM), and the
-// windows of one tile >= Np samples apart (M2 >= Np: every time point of the tile then sees the
-// same rotation s mod Np).  Tile shapes (Np, M1, Q): (64, 64..128, 1), (64, 256, 2),
-// (128, 64, 1), (128, 128, 2), (128, 256, 4), (256, 64, 2), (256, 128, 4).
+// M1 = max(64, N / 2048) (so M2 <= 2048 fits the second pass's tile: 512 threads, 4 columns, at
+// M2 = 2048), Q = Np M1 / 8192 CTAs per cluster (the block X_g(., k) takes 64 KB of shared memory
+// per CTA, two CTAs per SM), and the windows of one tile >= Np samples apart (M2 >= Np: every
+// time point of the tile then sees the same rotation s mod Np).  Tile shapes (Np, M1, Q):
+// (64, 64..128, 1), (64, 256, 2), (128, 64, 1), (128, 128, 2), (128, 256, 4), (256, 64, 2),
+// (256, 128, 4).  (M1 = 64 up to N = 2^17: the 64-point column pass costs less per point than a
+// 128-point one in a cluster, batch SSCA 20.80 -> 20.39 ms against M2 <= 1024.)
 struct FusedSplit {
   int M1, M2, Q;
 };
 inline bool fused_split(int64_t N, int Np, FusedSplit* s) {
   if (N < 4096 || N > (int64_t(1) << 20) || (N & (N - 1))) return false;
   if (Np != 64 && Np != 128 && Np != 256) return false;
-  int64_t M1 = N / 1024 > 64 ? N / 1024 : 64;
+  int64_t M1 = N / 2048 > 64 ? N / 2048 : 64;
   if (M1 > 256) return false;
   const int64_t Q = Np * M1 / 8192 > 1 ? Np * M1 / 8192 : 1;
   if (Q > 4) return false;
   const int64_t M2 = N / M1;
-  if (M2 < Np || M2 > 1024) return false;
+  if (M2 < Np || M2 > 2048) return false;
   s->M1 = (int)M1;
   s->M2 = (int)M2;
   s->Q = (int)Q;
@@ -55,9 +57,11 @@ inline bool fused_split(int64_t N, int Np, FusedSplit* s) {
 __host__ __device__ __forceinline__ int64_t yf_index(int m2, int q1, int M2, int C) {
   return (int64_t)(q1 / C) * M2 * C + (int64_t)m2 * C + (q1 % C);
 }
-// transforms per tile of the second pass for a runtime M2 (256 threads)
+// threads of a second-pass CTA (512 at M2 = 2048, so that a tile still holds 4 columns) and
+// transforms per tile for a runtime M2
+__host__ __device__ constexpr int rowsf_threads(int M2) { return M2 >= 2048 ? 512 : 256; }
 __host__ __device__ constexpr int rowsf_c(int M2) {
-  return M2 >= 1024 ? 8 : (M2 >= 256 ? 16 : 32);
+  return M2 >= 2048 ? 4 : (M2 >= 1024 ? 8 : (M2 >= 256 ? 16 : 32));
 }
 
 // t-fast transforms (a transform's threads consecutive, at most 32 of them): exchange stride
@@ -131,7 +135,7 @@ __device__ __forceinline__ void ssca_chancol_tile(float2* sm, const float2* __re
   float2* twm = reinterpret_cast<float2*>(base + Lay::twm_off);
   const int tid = threadIdx.x;
   const int CY = rowsf_c(M2);                           // Y's column blocks (yf_index)
-  const int lcy = CY == 8 ? 3 : (CY == 16 ? 4 : 5);
+  const int lcy = CY == 4 ? 2 : (CY == 8 ? 3 : (CY == 16 ? 4 : 5));
   const int smod = (m2 - NP / 2) & (NP - 1);            // s mod Np for every m1 (Np divides M2)
   if constexpr (Q > 1) cluster_arrive_relaxed();        // every CTA of the cluster has started ...
   for (int i = tid; i < M1; i += 256) rot[i] = __ldg(wN + (((int64_t)i * m2) & (N - 1)));   // W_N^{q1 m2}
@@ -213,7 +217,7 @@ template <int M2, bool PROF = false>
 __device__ __forceinline__ void ssca_rowsf_tile(float2* sm, const float2* __restrict__ Yk, float2* __restrict__ outk,
                                                 int M1, const float2* __restrict__ tw_m2, int q10,
                                                 float* prof = nullptr, int ah_off = 0, int power = 1) {
-  using S = TileShape<M2>;
+  using S = TileShape<M2, rowsf_threads(M2)>;
   constexpr int C = S::C;
   static_assert(C == rowsf_c(M2), "Y's column blocks are the second pass's tiles");
   const int c = (int)threadIdx.x % C;                   // interleaved: consecutive lanes, consecutive q1

@@ -31,10 +31,10 @@ def _rel(gpu, ref):
 
 
 # (N, Np): every (Np, M1, Q) tile shape (Q CTAs per cluster) and every second-pass size M2 in
-# 64 .. 1024
+# 64 .. 2048
 FULL = [(1 << 12, 64), (1 << 13, 128), (1 << 14, 128), (1 << 14, 256), (1 << 15, 128), (1 << 15, 64)]
 SAMPLED = [(1 << 16, 128), (1 << 16, 256), (1 << 17, 128), (1 << 17, 64), (1 << 17, 256), (1 << 18, 128),
-           (1 << 18, 64)]
+           (1 << 18, 64), (1 << 19, 128)]
 
 
 @pytest.mark.parametrize("N,Np", FULL)
@@ -89,7 +89,7 @@ def test_fused_variants(torch, variant):
     assert _rel(got, ref) <= FP32_TOL
 
 
-@pytest.mark.parametrize("N,Np", [(1 << 12, 32), (1 << 19, 128), (1 << 12, 128), (1 << 20, 64)])
+@pytest.mark.parametrize("N,Np", [(1 << 12, 32), (1 << 20, 128), (1 << 12, 128), (1 << 19, 256)])
 def test_fused_outside_its_tiles_runs_the_stages(torch, N, Np):
     x = signals.modulated("qpsk", N, 4, 0.02, 5.0, seed=2400 + Np)
     xd = _dev(torch, x)
