@@ -122,7 +122,7 @@ __global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(kThreads, 2)
 // ... and tile B = the M2-point pass over m2 for C consecutive q1 of one channel; PROF: each
 // bin reduced into the signal's alpha profile instead of stored.
 template <int M2, bool PROF>
-__global__ void __launch_bounds__(rowsf_threads(M2), M2 >= 1024 ? 2 : 3)
+__global__ void __launch_bounds__(rowsf_threads(M2), M2 >= 2048 ? 1 : (M2 >= 1024 ? 2 : 3))
     k_st_sfb(BatchArgs A, const Task* __restrict__ tl, int nt, int64_t total) {
   extern __shared__ __align__(128) float2 sm[];
   constexpr int C = rowsf_c(M2);

@@ -18,9 +18,10 @@ k_sf_chancol(const float2* __restrict__ x, const float2* __restrict__ y, int con
   ssca_chancol_tile<NP, M1, Q>(sm, x, y, conj != 0, N, M2, a, tw_np, tw_m1, wN, Y, m2, q);
 }
 
-// three CTAs per SM below M2 = 1024 (80 registers without spills); two at 1024
+// three CTAs per SM below M2 = 1024 (80 registers without spills); two at 1024; one of 1024
+// threads at 2048
 template <int M2>
-__global__ void __launch_bounds__(rowsf_threads(M2), M2 >= 1024 ? 2 : 3)
+__global__ void __launch_bounds__(rowsf_threads(M2), M2 >= 2048 ? 1 : (M2 >= 1024 ? 2 : 3))
 k_sf_rows(const float2* __restrict__ Y, int N, int M1, const float2* __restrict__ tw, float2* __restrict__ out) {
   extern __shared__ __align__(128) float2 sm[];
   const int64_t kh = blockIdx.y;

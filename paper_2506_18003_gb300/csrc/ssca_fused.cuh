@@ -28,7 +28,7 @@
 namespace scd {
 
 // The fused split of an SSCA strip transform, or false where the tiles do not fit:
-// M1 = max(64, N / 2048) (so M2 <= 2048 fits the second pass's tile: 512 threads, 4 columns, at
+// M1 = max(64, N / 2048) (so M2 <= 2048 fits the second pass's tile: 1024 threads, 8 columns, at
 // M2 = 2048), Q = Np M1 / 8192 CTAs per cluster (the block X_g(., k) takes 64 KB of shared memory
 // per CTA, two CTAs per SM), and the windows of one tile >= Np samples apart (M2 >= Np: every
 // time point of the tile then sees the same rotation s mod Np).  Tile shapes (Np, M1, Q):
@@ -57,11 +57,12 @@ inline bool fused_split(int64_t N, int Np, FusedSplit* s) {
 __host__ __device__ __forceinline__ int64_t yf_index(int m2, int q1, int M2, int C) {
   return (int64_t)(q1 / C) * M2 * C + (int64_t)m2 * C + (q1 % C);
 }
-// threads of a second-pass CTA (512 at M2 = 2048, so that a tile still holds 4 columns) and
-// transforms per tile for a runtime M2
-__host__ __device__ constexpr int rowsf_threads(int M2) { return M2 >= 2048 ? 512 : 256; }
+// threads of a second-pass CTA (1024 at M2 = 2048, one CTA per SM, so that a tile still holds 8
+// columns: tile A then writes Y in 64-byte runs, tile B writes S in 64-byte runs; 4 columns on
+// 512 threads measured 1.1% slower on the batch SSCA) and transforms per tile for a runtime M2
+__host__ __device__ constexpr int rowsf_threads(int M2) { return M2 >= 2048 ? 1024 : 256; }
 __host__ __device__ constexpr int rowsf_c(int M2) {
-  return M2 >= 2048 ? 4 : (M2 >= 1024 ? 8 : (M2 >= 256 ? 16 : 32));
+  return M2 >= 1024 ? 8 : (M2 >= 256 ? 16 : 32);
 }
 
 // t-fast transforms (a transform's threads consecutive, at most 32 of them): exchange stride
