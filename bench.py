@@ -427,34 +427,45 @@ class BatchWorkload:
                 ts += ev[1].elapsed_time(ev[2]) / reps
         binding.scd_check_device(stream)
         out_bytes = 4 * (plans[0][0].out_offsets[-1] + plans[1][0].out_offsets[-1])
-        # end to end in this output mode: input arena in from pinned host memory, both profile
-        # plans, both profile arenas out to pinned host memory, every step
-        xh = self.x.cpu().pin_memory()
-        hosts = [torch.empty(out.shape, dtype=out.dtype).pin_memory() for _, out in plans]
+        # end to end in this output mode, through scd_batch_run_host: the input arena in from
+        # page-locked host memory, both profile plans, both profile arenas out to page-locked host
+        # memory, every step; steps pipelined on two device output sets as in e2e()
+        hx = binding.HostBuffer(self.x.numel(), self.x.dtype)
+        hx.tensor.copy_(self.x.cpu())
+        hosts = [binding.HostBuffer(out.numel(), out.dtype) for _, out in plans]
+        second = [torch.empty_like(out) for _, out in plans]
 
-        def one():
-            self.x.copy_(xh, non_blocking=True)
-            for pl, out in plans:
-                pl.run(self.x, out, self.ws, stream=stream)
-            for h, (_, out) in zip(hosts, plans):
-                h.copy_(out, non_blocking=True)
+        def one(k):
+            for j, ((pl, out), h) in enumerate(zip(plans, hosts)):
+                pl.run_host(hx.tensor if j == 0 else None, self.x, out if k % 2 == 0 else second[j], h.tensor,
+                            self.ws, stream=stream)
+
+        def drain():
+            for pl, _ in plans:
+                pl.host_wait()
             stream.synchronize()
 
         with torch.cuda.stream(stream):
-            one()
+            one(0)
+            one(1)
+            drain()
             t0 = time.perf_counter()
-            for _ in range(reps):
-                one()
+            for k in range(reps):
+                one(k)
+            drain()
             dt = (time.perf_counter() - t0) / reps
         for pl, _ in plans:
             pl.close()
+        for h in [hx] + hosts:
+            h.close()
         return {"ms_per_step": round(tf + ts, 4), "stage_ms": {"fam_batch": round(tf, 4), "ssca_batch": round(ts, 4)},
                 "msamples_per_s": round(self.samples_per_step() / ((tf + ts) * 1e-3) / 1e6, 2),
                 "output_bytes_per_step": out_bytes,
                 "e2e": {"value": round(self.samples_per_step() / dt / 1e6, 2), "unit": "Msamples/s",
-                        "ms_per_step": round(dt * 1e3, 3), "h2d_bytes_per_step": xh.numel() * 8,
+                        "ms_per_step": round(dt * 1e3, 3), "h2d_bytes_per_step": self.x.numel() * 8,
                         "d2h_bytes_per_step": out_bytes,
-                        "api": "BatchPlan.run in alpha-profile mode with torch pinned-host copies in and out"},
+                        "api": "scd_batch_run_host (BatchPlan.run_host) in alpha-profile mode on page-locked host "
+                               "buffers; steps pipelined on two device output sets"},
                 "note": "alpha profiles (|S| max over f per alpha) fused into the last stage; FP32 form; tuned"}
 
     def exact_ssca(self, torch, binding, stream, reps=3):
@@ -486,28 +497,71 @@ class BatchWorkload:
         return res
 
     def e2e(self, prec, stream, steps, world, torch):
-        """H2D of the input arena from pinned memory, both batched estimates, D2H of both
-        output arenas into pinned memory, every step (public Python binding)."""
-        xh = self.x.cpu().pin_memory()
-        of = torch.empty(self.out_f.shape, dtype=self.out_f.dtype).pin_memory()
-        os_ = torch.empty(self.out_s.shape, dtype=self.out_s.dtype).pin_memory()
+        """Every step through the C ABI's host-buffer batch call (scd_batch_run_host, via
+        BatchPlan.run_host): H2D of the input arena from page-locked host memory, both batched
+        estimates, D2H of both output arenas into page-locked host memory (scd_host_alloc).
+        Measured twice: one step after the other (`serial`, each step waits for its copies), and
+        pipelined the way a stream of batches runs: the steps alternate between two device output
+        sets, so that step k's results travel to the host (on each plan's copy stream) while step
+        k + 1 computes; the timed region ends when the last step's results are in host memory."""
+        fam, ssca = self.plans[prec]
+        hx = self.binding.HostBuffer(self.x.numel(), self.x.dtype)
+        hf = self.binding.HostBuffer(self.out_f.numel(), self.out_f.dtype)
+        hs = self.binding.HostBuffer(self.out_s.numel(), self.out_s.dtype)
+        hx.tensor.copy_(self.x.cpu())                 # the input batch, resident in host memory
+        outs = [(self.out_f, self.out_s), (torch.empty_like(self.out_f), torch.empty_like(self.out_s))]
+        samples = world * self.samples_per_step() * steps
 
-        def one():
-            self.x.copy_(xh, non_blocking=True)
-            self.step(prec, stream)
-            of.copy_(self.out_f, non_blocking=True)
-            os_.copy_(self.out_s, non_blocking=True)
+        def one(k):
+            of, os_ = outs[k % 2]
+            fam.run_host(hx.tensor, self.x, of, hf.tensor, self.ws, stream=stream)
+            ssca.run_host(None, self.x, os_, hs.tensor, self.ws, stream=stream)
+
+        def drain():
+            fam.host_wait()
+            ssca.host_wait()
             stream.synchronize()
 
-        one()
-        barrier(world)
+        def timed(pipelined):
+            one(0)
+            one(1)
+            drain()
+            barrier(world)
+            t0 = time.perf_counter()
+            for k in range(steps):
+                one(k if pipelined else 0)
+                if not pipelined:
+                    drain()
+            drain()
+            return max_over_ranks(torch, time.perf_counter() - t0, world)
+
+        dt_serial = timed(False)
+        dt = timed(True)
+        # one more serial step with events between its parts (not part of either timing)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        fam.run_host(hx.tensor, self.x, self.out_f, hf.tensor, self.ws, stream=stream)
+        ev[1].record(stream)
+        ssca.run_host(None, self.x, self.out_s, hs.tensor, self.ws, stream=stream)
+        ev[2].record(stream)
         t0 = time.perf_counter()
-        for _ in range(steps):
-            one()
-        dt = max_over_ranks(torch, time.perf_counter() - t0, world)
-        return {"value": world * self.samples_per_step() * steps / dt / 1e6, "unit": "Msamples/s",
-                "h2d_bytes_per_step": xh.numel() * 8, "d2h_bytes_per_step": (of.numel() + os_.numel()) * 8,
-                "steps": steps, "api": "BatchPlan.run (scd_batch_run) with torch pinned-host copies in and out"}
+        drain()
+        parts = {"h2d_and_fam_ms": round(ev[0].elapsed_time(ev[1]), 2), "ssca_ms": round(ev[1].elapsed_time(ev[2]), 2),
+                 "copies_after_compute_ms": round((time.perf_counter() - t0) * 1e3, 2)}
+        d2h = (self.out_f.numel() + self.out_s.numel()) * 8
+        del outs
+        for h in (hx, hf, hs):
+            h.close()
+        torch.cuda.empty_cache()
+        return {"value": samples / dt / 1e6, "unit": "Msamples/s",
+                "h2d_bytes_per_step": self.x.numel() * 8, "d2h_bytes_per_step": d2h,
+                "steps": steps, "ms_per_step": round(dt / steps * 1e3, 3),
+                "d2h_gbs": round(d2h * steps / dt / 1e9, 1),
+                "serial": {"value": round(samples / dt_serial / 1e6, 2), "ms_per_step": round(dt_serial / steps * 1e3, 3),
+                           "parts": parts},
+                "api": "scd_batch_run_host (BatchPlan.run_host) on page-locked host buffers from scd_host_alloc; "
+                       "steps pipelined on two device output sets (step k's copies to the host while step k+1 "
+                       "computes); `serial`: each step waits for its own copies"}
 
 
 class PaperScaleWorkload:

@@ -247,6 +247,27 @@ SCD_API scd_status scd_batch_query(const scd_batch_plan* plan, int64_t* x_offset
 SCD_API scd_status scd_batch_run(scd_batch_plan* plan, const void* x_arena, const float* window, void* out_arena,
                                  void* workspace, void* stream);
 SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
+/* A run on host buffers, for batches that arrive from and return to host memory (the paper's
+ * setting of a front end that streams samples in and reads estimates out, Sec. I).  Copies the
+ * input arena from host memory x_host into the device arena x_dev (x_host NULL: x_dev already
+ * holds it), enqueues the run exactly as scd_batch_run (x_dev, window, out_dev, workspace, on
+ * `stream`), then copies out_dev into host memory out_host (the out arena's bytes: complex64, or
+ * float32 in an alpha-profile output mode) on the plan's own copy stream once the run is done.
+ * Asynchronous: returns when all of it is enqueued, so a following call with another out_dev
+ * computes while this call's results travel to the host; a call whose out_dev an earlier call
+ * used first waits (on the device) for that call's copy.  Successive calls must use the same
+ * `stream` (runs of one plan must not overlap).  scd_batch_host_wait blocks until every copy
+ * this plan queued has reached host memory.  Host buffers should be page-locked
+ * (scd_host_alloc) for full link bandwidth; pageable memory works but copies slower.  The
+ * plan keeps one event per distinct out_dev (freed by scd_batch_plan_destroy, which first
+ * waits for the plan's copies).  Errors as scd_batch_run; SCD_ERR_ARG for a NULL x_dev, out_dev
+ * or out_host; SCD_ERR_CUDA if a copy or event call fails (message in scd_last_error). */
+SCD_API scd_status scd_batch_run_host(scd_batch_plan* plan, const void* x_host, void* x_dev, const float* window,
+                                      void* out_dev, void* out_host, void* workspace, void* stream);
+SCD_API scd_status scd_batch_host_wait(scd_batch_plan* plan);
+/* Page-locked host memory (cudaHostAlloc) of `bytes` bytes, and its release; the caller owns it. */
+SCD_API scd_status scd_host_alloc(size_t bytes, void** ptr);
+SCD_API scd_status scd_host_free(void* ptr);
 /* Output of the plan's runs: mode 0 = the estimates (default); 1 / 2 = only each signal's
  * alpha profile of |S| / |S|^2 (scd_fam_alpha_profile / scd_ssca_alpha_profile of its
  * estimate, bit for bit), reduced inside the last stage so the estimate is never written

@@ -59,6 +59,10 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_size_t)]),
     "scd_batch_run": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "scd_batch_plan_destroy": (None, [_vp]),
+    "scd_batch_run_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "scd_batch_host_wait": (_i32, [_vp]),
+    "scd_host_alloc": (_i32, [_sz, ctypes.POINTER(_vp)]),
+    "scd_host_free": (_i32, [_vp]),
     "scd_batch_plan_set_output": (_i32, [_vp, _i32]),
     "scd_batch_plan_set_schedule": (_i32, [_vp, _i32]),
     "scd_batch_plan_create_exact": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_int64), _i32, _i32, _i32,
@@ -311,6 +315,33 @@ def scd_prepare(estimator: str, N: int, Np: int, P: int = 2) -> None:
     check(lib.scd_prepare({"fam": 0, "ssca": 1}[estimator], N, Np, P), "scd_prepare")
 
 
+class HostBuffer:
+    """Page-locked host memory (scd_host_alloc) of `numel` elements of `dtype`, viewed as the
+    CPU tensor `.tensor` (valid until close())."""
+
+    def __init__(self, numel, dtype):
+        torch = _torch()
+        self.lib = load()
+        nbytes = int(numel) * torch.empty((), dtype=dtype).element_size()
+        p = ctypes.c_void_p()
+        check(self.lib.scd_host_alloc(nbytes, ctypes.byref(p)), "scd_host_alloc")
+        self.ptr, self.nbytes = p.value, nbytes
+        buf = (ctypes.c_char * nbytes).from_address(self.ptr)
+        self.tensor = torch.frombuffer(buf, dtype=torch.uint8).view(dtype)
+
+    def close(self):
+        if self.ptr:
+            self.tensor = None
+            check(self.lib.scd_host_free(ctypes.c_void_p(self.ptr)), "scd_host_free")
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class BatchPlan:
     """A batch of uneven-length signals for one estimator (scd_batch_plan_* of the C ABI).
 
@@ -370,6 +401,27 @@ class BatchPlan:
         _need(out_arena, self.out_dtype(), self.out_offsets[-1], "out_arena")
         check(self.lib.scd_batch_run(self.handle, _ptr(x_arena), _ptr(window), _ptr(out_arena),
                                      _ptr(workspace), _stream(stream)), "scd_batch_run")
+
+    def run_host(self, x_host, x_arena, out_arena, out_host, workspace, window=None, stream=None):
+        """scd_batch_run_host: copies x_host (a CPU tensor, ideally a HostBuffer's; None when
+        x_arena already holds the input) into x_arena, runs the plan into out_arena and copies it
+        into out_host (a CPU tensor) on the plan's copy stream; returns once enqueued (host_wait)."""
+        torch = _torch()
+        _need(x_arena, torch.complex64, self.x_offsets[-1], "x_arena")
+        _need(out_arena, self.out_dtype(), self.out_offsets[-1], "out_arena")
+        for t, n, name in ((x_host, self.x_offsets[-1] * 8, "x_host"),
+                           (out_host, self.out_offsets[-1] * out_arena.element_size(), "out_host")):
+            if t is None and name == "x_host":
+                continue
+            if not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_contiguous() or \
+                    t.numel() * t.element_size() < n:
+                raise TypeError(f"{name} must be a contiguous CPU tensor of at least {n} bytes")
+        check(self.lib.scd_batch_run_host(self.handle, _ptr(x_host), _ptr(x_arena), _ptr(window), _ptr(out_arena),
+                                          _ptr(out_host), _ptr(workspace), _stream(stream)), "scd_batch_run_host")
+
+    def host_wait(self):
+        """Blocks until every copy run_host queued on this plan has reached host memory."""
+        check(self.lib.scd_batch_host_wait(self.handle), "scd_batch_host_wait")
 
     def tune(self, x_arena, out_arena, workspace, window=None, stream=None, reps=3):
         """Times the persistent schedule's sizing candidates on these buffers, keeps the fastest

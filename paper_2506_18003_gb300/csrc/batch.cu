@@ -106,26 +106,47 @@ struct scd_batch_plan {
   int bbytes_np = 0;
   const float* hamming = nullptr;
   unsigned* err = nullptr;
-  // cached graph of the last (x, window, out, workspace, stream) combination
-  cudaGraphExec_t exec = nullptr;
-  const void* g_x = nullptr;
-  const void* g_w = nullptr;
-  const void* g_out = nullptr;
-  const void* g_ws = nullptr;
-  void* g_stream = nullptr;
-  int g_drop = -1;
+  // cached graphs of the last two (x, window, out, workspace, stream) combinations (two, so that
+  // runs alternating between two output buffers replay their graphs)
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    const void* x = nullptr;
+    const void* w = nullptr;
+    const void* out = nullptr;
+    const void* ws = nullptr;
+    void* stream = nullptr;
+    int drop = -1;
+  };
+  Graph graphs[2];
+  int graph_next = 0;                     // the entry the next capture replaces
   // streaming plans (scd_stream_plan_create): window length and hop; 0 for batches
   int64_t stream_window = 0, stream_hop = 0;
   // output mode (scd_batch_plan_set_output): 0 full estimates, 1 / 2 alpha profiles of |S|^1 / |S|^2
   int prof_power = 0;
   int grid_prof = 0;                      // grid of the profile kernel (0: not prepared yet)
+  // runs on host buffers (scd_batch_run_host): the device-to-host copies run on the plan's own
+  // stream after the estimate; one event per output buffer marks the end of its last copy
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t computed = nullptr;
+  std::vector<std::pair<const void*, cudaEvent_t>> copied;
 };
 
 namespace {
 
+void drop_graphs(scd_batch_plan* p) {
+  for (auto& g : p->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = scd_batch_plan::Graph();
+  }
+}
+
 void free_plan(scd_batch_plan* p) {
   if (!p) return;
-  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->copy_st) cudaStreamSynchronize(p->copy_st);          // copies still reading the plan's buffers
+  for (auto& c : p->copied) cudaEventDestroy(c.second);
+  if (p->computed) cudaEventDestroy(p->computed);
+  if (p->copy_st) cudaStreamDestroy(p->copy_st);
+  drop_graphs(p);
   if (p->d_tasks) cudaFree(p->d_tasks);
   if (p->d_st) cudaFree(p->d_st);
   if (p->d_counters) cudaFree(p->d_counters);
@@ -284,7 +305,7 @@ scd_status build_tasks(scd_batch_plan* p) {
   }
   p->total = first;
   if (p->total >= (int64_t)0xFFFFFFF0u) return SCD_ERR_UNSUPPORTED;
-  if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+  drop_graphs(p);
   if (p->d_st) { cudaFree(p->d_st); p->d_st = nullptr; }
   p->st_tasks.clear();
   p->st_launches.clear();
@@ -832,9 +853,15 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
     e = launch_all();
     return e == cudaSuccess ? SCD_OK : cuda_status(e);
   }
-  if (!p->exec || p->g_x != x_arena || p->g_w != (const void*)w || p->g_out != out_arena || p->g_ws != workspace ||
-      p->g_stream != stream || p->g_drop != A.drop_task) {
-    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+  scd_batch_plan::Graph* gr = nullptr;
+  for (auto& c : p->graphs)
+    if (c.exec && c.x == x_arena && c.w == (const void*)w && c.out == out_arena && c.ws == workspace &&
+        c.stream == stream && c.drop == A.drop_task)
+      gr = &c;
+  if (!gr) {
+    gr = &p->graphs[p->graph_next];
+    p->graph_next ^= 1;
+    if (gr->exec) { cudaGraphExecDestroy(gr->exec); *gr = scd_batch_plan::Graph(); }
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return cuda_status(e);
     cudaError_t e1 = cudaMemsetAsync(p->d_counters, 0, cbytes, st);
@@ -843,17 +870,71 @@ scd_status scd_batch_run(scd_batch_plan* p, const void* x_arena, const float* wi
     e = cudaStreamEndCapture(st, &g);
     if (e1 != cudaSuccess) e = e1;
     if (e2 != cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gr->exec, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) { p->exec = nullptr; return cuda_status(e); }
-    p->g_x = x_arena; p->g_w = w; p->g_out = out_arena; p->g_ws = workspace; p->g_stream = stream;
-    p->g_drop = A.drop_task;
+    if (e != cudaSuccess) { gr->exec = nullptr; return cuda_status(e); }
+    gr->x = x_arena; gr->w = w; gr->out = out_arena; gr->ws = workspace; gr->stream = stream;
+    gr->drop = A.drop_task;
   }
-  e = cudaGraphLaunch(p->exec, st);
+  e = cudaGraphLaunch(gr->exec, st);
   return e == cudaSuccess ? SCD_OK : cuda_status(e);
 }
 
 void scd_batch_plan_destroy(scd_batch_plan* p) { free_plan(p); }
+
+scd_status scd_batch_run_host(scd_batch_plan* p, const void* x_host, void* x_dev, const float* window, void* out_dev,
+                              void* out_host, void* workspace, void* stream) {
+  using namespace scd;
+  NvtxRange range("scd_batch_run_host");
+  if (!p || !x_dev || !out_dev || !out_host) return SCD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!p->copy_st) {
+    if ((e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaEventCreateWithFlags(&p->computed, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+  }
+  cudaEvent_t done = nullptr;
+  for (auto& c : p->copied)
+    if (c.first == out_dev) done = c.second;
+  if (done) {
+    // the previous copy out of this buffer ends before the estimate overwrites it
+    if ((e = cudaStreamWaitEvent(st, done, 0)) != cudaSuccess) return cuda_status(e);
+  } else {
+    if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+    p->copied.emplace_back(out_dev, done);
+  }
+  const size_t xbytes = sizeof(float2) * (size_t)p->x_off[p->nsig];
+  const size_t obytes = (p->prof_power ? sizeof(float) : sizeof(float2)) * (size_t)p->out_off[p->nsig];
+  if (x_host && (e = cudaMemcpyAsync(x_dev, x_host, xbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_status(e);
+  const scd_status s = scd_batch_run(p, x_dev, window, out_dev, workspace, stream);
+  if (s != SCD_OK) return s;
+  if ((e = cudaEventRecord(p->computed, st)) != cudaSuccess || (e = cudaStreamWaitEvent(p->copy_st, p->computed, 0)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(out_host, out_dev, obytes, cudaMemcpyDeviceToHost, p->copy_st)) != cudaSuccess ||
+      (e = cudaEventRecord(done, p->copy_st)) != cudaSuccess)
+    return cuda_status(e);
+  return SCD_OK;
+}
+
+scd_status scd_batch_host_wait(scd_batch_plan* p) {
+  if (!p) return SCD_ERR_ARG;
+  if (!p->copy_st) return SCD_OK;
+  const cudaError_t e = cudaStreamSynchronize(p->copy_st);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
+}
+
+scd_status scd_host_alloc(size_t bytes, void** ptr) {
+  if (!ptr || bytes == 0) return SCD_ERR_ARG;
+  *ptr = nullptr;
+  const cudaError_t e = cudaHostAlloc(ptr, bytes, cudaHostAllocDefault);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
+}
+
+scd_status scd_host_free(void* ptr) {
+  if (!ptr) return SCD_OK;
+  const cudaError_t e = cudaFreeHost(ptr);
+  return e == cudaSuccess ? SCD_OK : cuda_status(e);
+}
 
 scd_status scd_batch_plan_set_output(scd_batch_plan* p, int32_t mode) {
   using namespace scd;
@@ -875,7 +956,7 @@ scd_status scd_batch_plan_set_output(scd_batch_plan* p, int32_t mode) {
   }
   p->prof_power = mode;
   layout_outputs(p);
-  if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+  drop_graphs(p);
   return build_tasks(p);
 }
 
