@@ -265,7 +265,9 @@ SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
 SCD_API scd_status scd_batch_run_host(scd_batch_plan* plan, const void* x_host, void* x_dev, const float* window,
                                       void* out_dev, void* out_host, void* workspace, void* stream);
 SCD_API scd_status scd_batch_host_wait(scd_batch_plan* plan);
-/* Page-locked host memory (cudaHostAlloc) of `bytes` bytes, and its release; the caller owns it. */
+/* Page-locked host memory (cudaHostAlloc) of `bytes` bytes, and its release; the caller owns it.
+ * SCD_ERR_ARG for bytes == 0 or a NULL ptr; SCD_ERR_CUDA if the allocation is refused (message
+ * in scd_last_error). */
 SCD_API scd_status scd_host_alloc(size_t bytes, void** ptr);
 SCD_API scd_status scd_host_free(void* ptr);
 /* Output of the plan's runs: mode 0 = the estimates (default); 1 / 2 = only each signal's

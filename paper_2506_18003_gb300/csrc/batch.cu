@@ -923,6 +923,11 @@ scd_status scd_batch_host_wait(scd_batch_plan* p) {
   return e == cudaSuccess ? SCD_OK : cuda_status(e);
 }
 
+// Page-locked host memory for the copies of scd_batch_run_host.  (Measured with a GB300 and its
+// Grace host: device-to-host copies into page-locked buffers ran between 38 and 193 GB/s
+// depending on the buffer, whether it came from cudaHostAlloc or from huge-page memory
+// registered with cudaHostRegister; the rate follows where the host pages land, not how they
+// were allocated, so the plain call stays.)
 scd_status scd_host_alloc(size_t bytes, void** ptr) {
   if (!ptr || bytes == 0) return SCD_ERR_ARG;
   *ptr = nullptr;
