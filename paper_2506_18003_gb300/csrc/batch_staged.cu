@@ -160,14 +160,16 @@ __global__ void __launch_bounds__(kThreads) k_st_fchan(BatchArgs A, const Task* 
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-// FAM pair transforms of one size class P, the FP32 form's registers capped as the standalone
-// pair kernel's (fam.cu): 3 CTAs per SM at P = 512 and 1024, 4 at 2048 and 4096, 2 at 8192.
-template <int PP, bool TC>
+// FAM pair transforms of one size class P, the FP32 form's registers capped for 3 CTAs per SM at
+// P = 512 and 1024, 4 at 2048 and 4096, 3 at 8192 (80 registers, 44 bytes of spills: the FAM
+// batch 11.03 -> 10.60 ms against 2 CTAs of 128 registers) except in the profile mode, whose
+// reduction needs more registers there (2).
+template <int PP, bool TC, bool PROF>
 __host__ __device__ constexpr int fpairs_minb() {
-  return TC ? 1 : (PP == 8192 ? 2 : (PP >= 2048 ? 4 : (PP >= 512 ? 3 : 1)));
+  return TC ? 1 : (PP == 8192 ? (PROF ? 2 : 3) : (PP >= 2048 ? 4 : (PP >= 512 ? 3 : 1)));
 }
 template <int PP, bool TC, bool PROF>
-__global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC>()) k_st_fpairs(BatchArgs A, const Task* __restrict__ tl,
+__global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC, PROF>()) k_st_fpairs(BatchArgs A, const Task* __restrict__ tl,
                                                                               int nt, int64_t total) {
   extern __shared__ __align__(128) float2 sm[];
   using S = TileShape<PP>;
