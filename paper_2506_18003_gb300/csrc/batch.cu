@@ -889,9 +889,13 @@ scd_status scd_batch_run_host(scd_batch_plan* p, const void* x_host, void* x_dev
   if (!p || !x_dev || !out_dev || !out_host) return SCD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (!p->copy_st) {
-    if ((e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaEventCreateWithFlags(&p->computed, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+  if (!p->copy_st && (e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking)) != cudaSuccess) {
+    p->copy_st = nullptr;
+    return cuda_status(e);
+  }
+  if (!p->computed && (e = cudaEventCreateWithFlags(&p->computed, cudaEventDisableTiming)) != cudaSuccess) {
+    p->computed = nullptr;
+    return cuda_status(e);
   }
   cudaEvent_t done = nullptr;
   for (auto& c : p->copied)
@@ -901,7 +905,7 @@ scd_status scd_batch_run_host(scd_batch_plan* p, const void* x_host, void* x_dev
     if ((e = cudaStreamWaitEvent(st, done, 0)) != cudaSuccess) return cuda_status(e);
   } else {
     if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
-    p->copied.emplace_back(out_dev, done);
+    p->copied.emplace_back(out_dev, done);           // (waited on only once a copy has been recorded)
   }
   const size_t xbytes = sizeof(float2) * (size_t)p->x_off[p->nsig];
   const size_t obytes = (p->prof_power ? sizeof(float) : sizeof(float2)) * (size_t)p->out_off[p->nsig];
