@@ -160,14 +160,15 @@ __global__ void __launch_bounds__(kThreads) k_st_fchan(BatchArgs A, const Task* 
   if constexpr (TC) tc_end<FS::tmem_cols>(ctx);
 }
 
-// FAM pair transforms of one size class P, the FP32 form's registers capped for 3 CTAs per SM at
-// P = 512 and 1024, 4 at 2048 and 4096, 3 at 8192 (80 registers, 44 bytes of spills: the FAM
-// batch 11.03 -> 10.60 ms against 2 CTAs of 128 registers) except in the profile mode, whose
-// reduction needs more registers there (2); the split form at 2 CTAs per SM (128 registers
-// instead of up to 221: its staged FAM batch 23.97 -> 19.87 ms).
+// FAM pair transforms of one size class P, the FP32 form's registers capped for 2 CTAs per SM at
+// P = 512 and 1024 (128 registers; 3 at 80 measured 0.3% slower on the FAM batch), 4 at 2048 and
+// 4096, 3 at 8192 (80 registers, 44 bytes of spills: the FAM batch 11.03 -> 10.60 ms against 2
+// CTAs of 128 registers) except in the profile mode, whose reduction needs more registers there
+// (2); the split form at 2 CTAs per SM (128 registers instead of up to 221: its staged FAM batch
+// 23.97 -> 19.87 ms).
 template <int PP, bool TC, bool PROF>
 __host__ __device__ constexpr int fpairs_minb() {
-  return TC ? 2 : (PP == 8192 ? (PROF ? 2 : 3) : (PP >= 2048 ? 4 : (PP >= 512 ? 3 : 1)));
+  return TC ? 2 : (PP == 8192 ? (PROF ? 2 : 3) : (PP >= 2048 ? 4 : (PP >= 512 ? 2 : 1)));
 }
 template <int PP, bool TC, bool PROF>
 __global__ void __launch_bounds__(kThreads, fpairs_minb<PP, TC, PROF>()) k_st_fpairs(BatchArgs A, const Task* __restrict__ tl,
