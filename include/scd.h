@@ -261,8 +261,10 @@ SCD_API void scd_batch_plan_destroy(scd_batch_plan* plan);
  * (scd_host_alloc) for full link bandwidth; pageable memory works but copies slower.  x_dev,
  * out_dev, out_host and x_host must stay valid until the copies are done (scd_batch_host_wait),
  * as for any asynchronous call.  The plan keeps one event per distinct out_dev (freed by
- * scd_batch_plan_destroy, which first waits for the plan's copies).  Errors as scd_batch_run; SCD_ERR_ARG for a NULL x_dev, out_dev
- * or out_host; SCD_ERR_CUDA if a copy or event call fails (message in scd_last_error). */
+ * scd_batch_plan_destroy, which first waits for the plan's copies).  Errors as scd_batch_run
+ * (its argument checks come first, so an argument error enqueues nothing); SCD_ERR_ARG for a
+ * NULL x_dev, out_dev or out_host; SCD_ERR_CUDA if a copy or event call fails (message in
+ * scd_last_error). */
 SCD_API scd_status scd_batch_run_host(scd_batch_plan* plan, const void* x_host, void* x_dev, const float* window,
                                       void* out_dev, void* out_host, void* workspace, void* stream);
 SCD_API scd_status scd_batch_host_wait(scd_batch_plan* plan);

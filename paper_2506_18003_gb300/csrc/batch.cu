@@ -886,9 +886,16 @@ scd_status scd_batch_run_host(scd_batch_plan* p, const void* x_host, void* x_dev
                               void* out_host, void* workspace, void* stream) {
   using namespace scd;
   NvtxRange range("scd_batch_run_host");
-  if (!p || !x_dev || !out_dev || !out_host) return SCD_ERR_ARG;
+  if (!p || !x_dev || !out_dev || !out_host || !workspace) return SCD_ERR_ARG;
+  // the argument checks of scd_batch_run, before anything is enqueued or created
+  if (((uintptr_t)x_dev % 8) || ((uintptr_t)out_dev % 16) || ((uintptr_t)workspace % 16) ||
+      (window && ((uintptr_t)window % 4)))
+    return SCD_ERR_ARG;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev != p->device) return SCD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaSuccess;
   if (!p->copy_st && (e = cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking)) != cudaSuccess) {
     p->copy_st = nullptr;
     return cuda_status(e);
