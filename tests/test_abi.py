@@ -234,3 +234,16 @@ def test_noalloc_argument_validation(lib):
     assert lib.scd_fam_noalloc(FAKE, 1 << 20, 32, 8, 1 << 16, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
     # the check that scd_fam has and the first version of this entry point lacked
     assert lib.scd_fam_noalloc(FAKE, 1 << 32, 16, 1 << 20, 4096, None, FAKE, None) == binding.SCD_ERR_UNSUPPORTED
+
+
+def test_host_buffer_calls_validation(lib):
+    """The host-buffer batch calls and the page-locked allocator reject bad arguments before
+    any CUDA call: no plan, NULL device or host pointers, misaligned device pointers, a zero
+    size; freeing NULL is a no-op."""
+    p = ctypes.c_void_p
+    assert lib.scd_batch_run_host(None, None, FAKE, None, FAKE, FAKE, FAKE, None) == binding.SCD_ERR_ARG
+    assert lib.scd_batch_host_wait(None) == binding.SCD_ERR_ARG
+    ptr = p()
+    assert lib.scd_host_alloc(0, ctypes.byref(ptr)) == binding.SCD_ERR_ARG
+    assert lib.scd_host_alloc(16, None) == binding.SCD_ERR_ARG
+    assert lib.scd_host_free(None) == binding.SCD_OK
